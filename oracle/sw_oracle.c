@@ -1,0 +1,452 @@
+/*
+ * Swendsen-Wang oracle: a plain, single-threaded CPU implementation of one
+ * SW sweep for the 2D/3D Ising, q-state Potts and classical XY models
+ * (Komura & Okabe, "CUDA programs for GPU computing of Swendsen-Wang
+ * multi-cluster spin flip algorithm", Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The product path
+ * (the CUDA library and its Python binding) never calls it, and this file
+ * shares no code, header, table or constant with that path.
+ *
+ * Every step follows the paper's three SW steps in the paper's order
+ * (Sec. 2: (1) active bond generation, (2) cluster labeling, (3) spin flip)
+ * followed by the measurement of M and E (Sec. 2, Eqs. for M and the Potts
+ * M^2).  Where the paper leaves a choice open the reading taken is stated at
+ * the function.  Floating point is IEEE double except where a float decides
+ * an integer (the XY bond test), which is taken in float as the kernels do.
+ *
+ * Lattice conventions: N = L^D sites, site i = x + L*(y + L*z), x fastest,
+ * periodic boundaries (Sec. 1, below the Ising Hamiltonian).  Bond (i,d)
+ * joins i and its +d neighbour.  J = 1.
+ *
+ * Bond bit-planes: plane d holds one bit per site for bond (i,d); each
+ * lattice row (fixed y,z) is padded to W = ceil(L/32) 32-bit words; word
+ * index = d*(R*W) + row*W + (x>>5), bit x&31, with R = L^(D-1) rows and
+ * row = y + L*z.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11), key = (seed low, seed high),
+ * counter = (site, sweep, purpose, 0).  The paper uses an LCG and says any
+ * other generator may be used (Sec. 2, technical remarks).
+ *   purpose 0 (INIT): initial state, word 0
+ *   purpose 1 (BOND): words 0..D-1 decide bonds (i,d); word D is site i's
+ *                     cluster draw, used when i is the root of its cluster
+ *   purpose 3 (AXIS): counter (0, sweep, 3, 0), word 0 -> XY mirror angle
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_ISING 0
+#define OR_POTTS 1
+#define OR_XY 2
+
+#define PURPOSE_INIT 0u
+#define PURPOSE_BOND 1u
+#define PURPOSE_AXIS 3u
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, written from the definition in Salmon et al. (SC'11),
+ * Sec. 3: ten rounds of two 32x32->64 multiplications whose high halves are
+ * xor-ed with the other counter words and the round key; the key is bumped
+ * by the Weyl constants between rounds. */
+static const uint32_t PHILOX_M0 = 0xD2511F53u;
+static const uint32_t PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u; /* golden ratio */
+static const uint32_t PHILOX_W1 = 0xBB67AE85u; /* sqrt(3) - 1 */
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw4(uint64_t seed, uint32_t site, uint32_t sweep, uint32_t purpose,
+                  uint32_t w[4]) {
+  uint32_t ctr[4] = {site, sweep, purpose, 0u};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  oracle_philox4x32_10(ctr, key, w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry helpers. */
+static int64_t n_sites(int dim, int L) {
+  int64_t n = 1;
+  for (int d = 0; d < dim; ++d) n *= L;
+  return n;
+}
+
+static int64_t row_words(int L) { return (L + 31) / 32; }
+
+int64_t oracle_plane_words(int dim, int L) {
+  return (int64_t)dim * n_sites(dim - 1, L) * row_words(L);
+}
+
+/* +d neighbour of site i with periodic wrap. */
+static int64_t neighbour(int dim, int L, int64_t i, int d) {
+  int64_t x = i % L;
+  int64_t y = (i / L) % L;
+  int64_t z = (dim == 3) ? i / ((int64_t)L * L) : 0;
+  if (d == 0) x = (x + 1) % L;
+  if (d == 1) y = (y + 1) % L;
+  if (d == 2) z = (z + 1) % L;
+  return x + (int64_t)L * (y + (int64_t)L * z);
+}
+
+static int64_t plane_word_index(int dim, int L, int64_t i, int d) {
+  int64_t x = i % L;
+  int64_t row = i / L;
+  int64_t R = n_sites(dim - 1, L);
+  return (int64_t)d * R * row_words(L) + row * row_words(L) + (x >> 5);
+}
+
+static int plane_bit(const uint32_t* planes, int dim, int L, int64_t i, int d) {
+  return (int)((planes[plane_word_index(dim, L, i, d)] >> ((i % L) & 31)) & 1u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bond probability (Sec. 2, step (1)).  The printed formula
+ * p = 1 - e^{2J/T} has lost its minus sign; the Ising SW probability is
+ * p = 1 - exp(-2J/T).  For the Potts Hamiltonian H = -J sum(delta - 1)
+ * (Sec. 1) the same construction gives p = 1 - exp(-J/T).  The bond test
+ * is taken on integers: active iff the 32-bit draw u < t with
+ * t = floor(p * 2^32), p evaluated in double as -expm1(-a). */
+uint32_t oracle_bond_threshold(int model, double T) {
+  double a = (model == OR_ISING) ? 2.0 / T : 1.0 / T;
+  double p = -expm1(-a);
+  double t = floor(p * 4294967296.0);
+  if (t > 4294967295.0) t = 4294967295.0;
+  if (t < 0.0) t = 0.0;
+  return (uint32_t)t;
+}
+
+/* XY mirror angle for sweep k (Sec. 2, remark on ispr: one random direction
+ * shared by all sites): phi = (w0 >> 8) * (2 pi / 2^24), taken in float. */
+float oracle_xy_phi(uint64_t seed, uint32_t sweep) {
+  uint32_t w[4];
+  draw4(seed, 0u, sweep, PURPOSE_AXIS, w);
+  const float step = (float)(6.283185307179586476925 / 16777216.0);
+  return (float)(w[0] >> 8) * step;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial configuration (paper: device_function_spinset; the distribution is
+ * not stated, a uniformly random start is taken). */
+int oracle_init(int model, int dim, int L, int q, uint64_t seed, void* spins) {
+  int64_t N = n_sites(dim, L);
+  const float step = (float)(6.283185307179586476925 / 16777216.0);
+  for (int64_t i = 0; i < N; ++i) {
+    uint32_t w[4];
+    draw4(seed, (uint32_t)i, 0u, PURPOSE_INIT, w);
+    if (model == OR_ISING) {
+      ((int8_t*)spins)[i] = (w[0] >> 31) ? (int8_t)-1 : (int8_t)1;
+    } else if (model == OR_POTTS) {
+      ((uint8_t*)spins)[i] = (uint8_t)(((uint64_t)w[0] * (uint64_t)q) >> 32);
+    } else {
+      ((float*)spins)[i] = (float)(w[0] >> 8) * step;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step (1): active bond generation (Sec. 2).
+ * Ising/Potts: bond (i,j) active iff s_i == s_j and u_d < t.
+ * XY (embedded Ising clusters, Wolff 1989; Sec. 1 and Sec. 2 remarks on the
+ * clock model): project on r = (cos phi, sin phi): x_i = cos(theta_i - phi);
+ * bond active iff x_i x_j > 0 and u < 1 - exp(-2K x_i x_j), with
+ * u = (w_d >> 8) 2^-24.  Taken in float (the decision is an integer). */
+void oracle_bonds(int model, int dim, int L, int q, double T, uint64_t seed,
+                  uint32_t sweep, const void* spins, uint32_t* planes) {
+  (void)q;
+  int64_t N = n_sites(dim, L);
+  memset(planes, 0, sizeof(uint32_t) * (size_t)oracle_plane_words(dim, L));
+  uint32_t t = (model == OR_XY) ? 0u : oracle_bond_threshold(model, T);
+  float phi = (model == OR_XY) ? oracle_xy_phi(seed, sweep) : 0.0f;
+  float twoK = (float)(2.0 / T);
+  for (int64_t i = 0; i < N; ++i) {
+    uint32_t w[4];
+    draw4(seed, (uint32_t)i, sweep, PURPOSE_BOND, w);
+    for (int d = 0; d < dim; ++d) {
+      int64_t j = neighbour(dim, L, i, d);
+      int active = 0;
+      if (model == OR_ISING) {
+        active = (((const int8_t*)spins)[i] == ((const int8_t*)spins)[j]) && (w[d] < t);
+      } else if (model == OR_POTTS) {
+        active = (((const uint8_t*)spins)[i] == ((const uint8_t*)spins)[j]) && (w[d] < t);
+      } else {
+        float ti = ((const float*)spins)[i];
+        float tj = ((const float*)spins)[j];
+        float xi = cosf(ti - phi);
+        float xj = cosf(tj - phi);
+        float prod = xi * xj;
+        if (prod > 0.0f) {
+          float p = -expm1f(-(twoK * prod));
+          float u = (float)(w[d] >> 8) * 0x1p-24f;
+          active = u < p;
+        }
+      }
+      if (active) planes[plane_word_index(dim, L, i, d)] |= 1u << ((i % L) & 31);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step (2): cluster labeling (Sec. 2).  Sequential union-find, the class the
+ * paper cites as the CPU standard (Hoshen-Kopelman); the larger root is
+ * always linked under the smaller one, so every root is the smallest site
+ * index of its tree and label[i] = find(i) is the minimum site index of i's
+ * cluster. */
+static int64_t uf_find(int64_t* parent, int64_t x) {
+  while (parent[x] != x) {
+    parent[x] = parent[parent[x]]; /* path halving */
+    x = parent[x];
+  }
+  return x;
+}
+
+static void uf_unite(int64_t* parent, int64_t a, int64_t b) {
+  a = uf_find(parent, a);
+  b = uf_find(parent, b);
+  if (a == b) return;
+  if (a < b) parent[b] = a;
+  else parent[a] = b;
+}
+
+int oracle_labels(int dim, int L, const uint32_t* planes, int32_t* labels) {
+  int64_t N = n_sites(dim, L);
+  int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  if (!parent) return -1;
+  for (int64_t i = 0; i < N; ++i) parent[i] = i;
+  for (int64_t i = 0; i < N; ++i)
+    for (int d = 0; d < dim; ++d)
+      if (plane_bit(planes, dim, L, i, d)) uf_unite(parent, i, neighbour(dim, L, i, d));
+  for (int64_t i = 0; i < N; ++i) labels[i] = (int32_t)uf_find(parent, i);
+  free(parent);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step (3): spin flip (Sec. 2; paper: spin_select then spin_flip).  Each
+ * cluster takes one new state, drawn from word D of its root's BOND draw:
+ *   Ising: +1 if w < 2^31 else -1   (set at random, Sec. 2 step (3))
+ *   Potts: floor(w q / 2^32)        (uniform of q states)
+ *   XY:    reflect about the line perpendicular to r iff w >= 2^31:
+ *          theta' = 2 phi + pi - theta, wrapped to [0, 2 pi)  (Wolff's
+ *          embedded-cluster flip).
+ * Returns the number of clusters (roots). */
+int64_t oracle_flip(int model, int dim, int L, int q, uint64_t seed, uint32_t sweep,
+                    const int32_t* labels, void* spins) {
+  int64_t N = n_sites(dim, L);
+  int64_t nclusters = 0;
+  uint32_t* root_draw = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  if (!root_draw) return -1;
+  for (int64_t r = 0; r < N; ++r) {
+    if (labels[r] != r) continue;
+    uint32_t w[4];
+    draw4(seed, (uint32_t)r, sweep, PURPOSE_BOND, w);
+    root_draw[r] = w[dim];
+    ++nclusters;
+  }
+  double phi = (model == OR_XY) ? (double)oracle_xy_phi(seed, sweep) : 0.0;
+  const double two_pi = 6.283185307179586476925;
+  const double pi = 3.141592653589793238463;
+  for (int64_t i = 0; i < N; ++i) {
+    uint32_t w = root_draw[labels[i]];
+    if (model == OR_ISING) {
+      ((int8_t*)spins)[i] = (w >> 31) ? (int8_t)-1 : (int8_t)1;
+    } else if (model == OR_POTTS) {
+      ((uint8_t*)spins)[i] = (uint8_t)(((uint64_t)w * (uint64_t)q) >> 32);
+    } else if (w >> 31) {
+      double th = 2.0 * phi + pi - (double)((float*)spins)[i];
+      while (th >= two_pi) th -= two_pi;
+      while (th < 0.0) th += two_pi;
+      ((float*)spins)[i] = (float)th;
+    }
+  }
+  free(root_draw);
+  return nclusters;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Measurement (Sec. 2: M = sum s_i and the energy; Potts M^2 equation).
+ *   Ising: M = sum s_i, E = -sum_<ij> s_i s_j, M2 = M^2
+ *   Potts: n[k] histogram, S2 = sum n[k]^2, M2 = (q S2 - N^2)/(q-1),
+ *          E = sum_<ij> (1 - delta(s_i,s_j))   (the paper's H with J = 1)
+ *   XY:    mx = sum cos, my = sum sin, M2 = mx^2 + my^2,
+ *          E = -sum_<ij> cos(theta_i - theta_j)
+ * The quartic moment is M4 = (M2)^2 for every model (for Potts the paper
+ * gives M^2 only; squaring it reduces to the Ising M^4 at q = 2). */
+typedef struct {
+  int64_t M;
+  int64_t E;
+  int64_t nclusters;
+  int64_t S2;
+  double mx;
+  double my;
+  double e_xy;
+  double M2;
+  double Ed;
+} oracle_record;
+
+void oracle_moments(int model, int dim, int L, int q, const void* spins,
+                    oracle_record* rec) {
+  int64_t N = n_sites(dim, L);
+  memset(rec, 0, sizeof(*rec));
+  if (model == OR_ISING) {
+    const int8_t* s = (const int8_t*)spins;
+    int64_t M = 0, E = 0;
+    for (int64_t i = 0; i < N; ++i) {
+      M += s[i];
+      for (int d = 0; d < dim; ++d) E -= (int64_t)s[i] * s[neighbour(dim, L, i, d)];
+    }
+    rec->M = M;
+    rec->E = E;
+    rec->M2 = (double)M * (double)M;
+    rec->Ed = (double)E;
+  } else if (model == OR_POTTS) {
+    const uint8_t* s = (const uint8_t*)spins;
+    int64_t* n = (int64_t*)calloc((size_t)q, sizeof(int64_t));
+    int64_t E = 0;
+    for (int64_t i = 0; i < N; ++i) {
+      n[s[i]] += 1;
+      for (int d = 0; d < dim; ++d) E += (s[i] != s[neighbour(dim, L, i, d)]) ? 1 : 0;
+    }
+    int64_t S2 = 0;
+    for (int k = 0; k < q; ++k) S2 += n[k] * n[k];
+    free(n);
+    rec->S2 = S2;
+    rec->E = E;
+    rec->M2 = (double)((int64_t)q * S2 - N * N) / (double)(q - 1);
+    rec->Ed = (double)E;
+  } else {
+    const float* th = (const float*)spins;
+    double mx = 0.0, my = 0.0, e = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      mx += cos((double)th[i]);
+      my += sin((double)th[i]);
+      for (int d = 0; d < dim; ++d)
+        e -= cos((double)th[i] - (double)th[neighbour(dim, L, i, d)]);
+    }
+    rec->mx = mx;
+    rec->my = my;
+    rec->e_xy = e;
+    rec->M2 = mx * mx + my * my;
+    rec->Ed = e;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* A whole run: the sample program's main loop (Sec. 2: mcs1 discarded
+ * sweeps, mcs2 measured sweeps), accumulating sum M^2, M^4, E, E^2 and the
+ * cluster count over measured sweeps in double, in sweep order. */
+typedef struct {
+  double n_sweeps;
+  double sum_M2;
+  double sum_M4;
+  double sum_E;
+  double sum_E2;
+  double sum_nclusters;
+} oracle_acc;
+
+typedef struct {
+  int model, dim, L, q;
+  double T;
+  uint64_t seed;
+  int64_t N;
+  uint32_t sweep;
+  void* spins;
+  uint32_t* planes;
+  int32_t* labels;
+  oracle_record last;
+  oracle_acc acc;
+} oracle_sw;
+
+static size_t spin_bytes(int model) { return model == OR_XY ? sizeof(float) : 1; }
+
+oracle_sw* oracle_create(int model, int dim, int L, int q, double T, uint64_t seed) {
+  if (model < 0 || model > 2 || dim < 2 || dim > 3 || L < 2 || !(T > 0.0)) return NULL;
+  if (model == OR_POTTS && (q < 2 || q > 256)) return NULL;
+  oracle_sw* o = (oracle_sw*)calloc(1, sizeof(oracle_sw));
+  if (!o) return NULL;
+  o->model = model; o->dim = dim; o->L = L; o->q = (model == OR_POTTS) ? q : 2;
+  o->T = T; o->seed = seed; o->N = n_sites(dim, L); o->sweep = 0;
+  o->spins = calloc((size_t)o->N, spin_bytes(model));
+  o->planes = (uint32_t*)calloc((size_t)oracle_plane_words(dim, L), sizeof(uint32_t));
+  o->labels = (int32_t*)calloc((size_t)o->N, sizeof(int32_t));
+  if (!o->spins || !o->planes || !o->labels) {
+    free(o->spins); free(o->planes); free(o->labels); free(o);
+    return NULL;
+  }
+  oracle_init(model, dim, L, o->q, seed, o->spins);
+  return o;
+}
+
+void oracle_destroy(oracle_sw* o) {
+  if (!o) return;
+  free(o->spins); free(o->planes); free(o->labels); free(o);
+}
+
+static void accumulate(oracle_acc* a, const oracle_record* r) {
+  double m2 = r->M2;
+  double e = r->Ed;
+  a->n_sweeps += 1.0;
+  a->sum_M2 += m2;
+  a->sum_M4 += m2 * m2;
+  a->sum_E += e;
+  a->sum_E2 += e * e;
+  a->sum_nclusters += (double)r->nclusters;
+}
+
+/* One sweep with an optionally injected bond mask (NULL: draw the bonds). */
+int oracle_sweep_with_planes(oracle_sw* o, const uint32_t* planes_in, int measure) {
+  o->sweep += 1;
+  if (planes_in)
+    memcpy(o->planes, planes_in, sizeof(uint32_t) * (size_t)oracle_plane_words(o->dim, o->L));
+  else
+    oracle_bonds(o->model, o->dim, o->L, o->q, o->T, o->seed, o->sweep, o->spins, o->planes);
+  if (oracle_labels(o->dim, o->L, o->planes, o->labels) != 0) return -1;
+  int64_t ncl = oracle_flip(o->model, o->dim, o->L, o->q, o->seed, o->sweep, o->labels, o->spins);
+  if (ncl < 0) return -1;
+  if (measure) {
+    oracle_moments(o->model, o->dim, o->L, o->q, o->spins, &o->last);
+    o->last.nclusters = ncl;
+    accumulate(&o->acc, &o->last);
+  }
+  return 0;
+}
+
+int oracle_sweep(oracle_sw* o, int n, int measure) {
+  for (int k = 0; k < n; ++k)
+    if (oracle_sweep_with_planes(o, NULL, measure) != 0) return -1;
+  return 0;
+}
+
+void* oracle_spins(oracle_sw* o) { return o->spins; }
+uint32_t* oracle_planes(oracle_sw* o) { return o->planes; }
+int32_t* oracle_label_array(oracle_sw* o) { return o->labels; }
+uint32_t oracle_sweep_counter(oracle_sw* o) { return o->sweep; }
+void oracle_set_sweep_counter(oracle_sw* o, uint32_t k) { o->sweep = k; }
+void oracle_last_record(oracle_sw* o, oracle_record* out) { *out = o->last; }
+void oracle_take_acc(oracle_sw* o, oracle_acc* out) {
+  *out = o->acc;
+  memset(&o->acc, 0, sizeof(o->acc));
+}
