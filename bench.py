@@ -1,0 +1,308 @@
+"""Benchmark of the Swendsen-Wang sweep on GB300.
+
+Workload: 3D Ising, simple cubic L=256 periodic (16,777,216 sites), J=1,
+K=0.2216546 (T=1/K), random start from seed 1001, 100 discarded sweeps
+before timing.  One step = one measured SW sweep (Philox bonds + tile
+labels, boundary merge, flip, moment reduction).  Metric: site-updates per
+nanosecond = sites x steps / device time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Timing: CUDA events on the library's stream around every step, the L2
+flushed (a 512 MiB write) between timed steps, untimed; K steps bracketed by
+a barrier and torch.cuda.synchronize(); the max over ranks.  N > 1 runs N
+independent replicas (one lattice per GPU, seed 1001 + rank): the sweep of
+one lattice does not shard.  The reference arm times the CPU oracle (single
+thread) on the same workload, over a bounded number of sweeps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+METRIC = "SW site-updates/ns (3D Ising L=256) vs HBM roofline; served mix jobs/s, p50/p99"
+UNIT = "site-updates/ns"
+MODEL, DIM, L, Q = 0, 3, 256, 2
+K_COUPLING = 0.2216546
+T = 1.0 / K_COUPLING
+SEED = 1001
+DISCARD = 100
+N_SITES = L ** DIM
+WORKLOAD = {"workload": "3D Ising SW sweep, simple cubic L=256 periodic, K=0.2216546, "
+                        "int8 spins, random start (seed 1001), 100 discarded sweeps, "
+                        "measured sweeps (bonds+labels+flip+moments)",
+            "model": "ising", "dim": 3, "L": L, "sites": N_SITES, "T": T,
+            "l2": "flushed between timed steps (512 MiB write)"}
+
+# Algorithmic bytes per site per sweep of each kernel (3D Ising), the
+# minimum each must move: bond+tile-label reads the spin (1 B) and writes
+# the bond bits (3/8 B) and the forest word (4 B); flip reads the forest
+# word (4 B) and writes the spin (1 B); measurement reads the spin (1 B).
+# The merge touches only tile faces and is given per face bond instead.
+KERNEL_BYTES_PER_SITE = {"bond_label": 1 + 3 / 8 + 4, "merge": None, "flip": 4 + 1, "measure": 1}
+PHASES = ["bond_label", "merge", "flip", "measure"]
+# Reference bytes model: 10.75 B/site/sweep for 3D Ising (bond 1.375,
+# tile label 4.375, flip 5), independent of the schedule.
+B_REF = 10.75
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(world: int, sites_per_rank: int, steps: int, max_seconds: float) -> float:
+    """Whole-job site-updates/ns: every rank's sites x steps over the
+    slowest rank's time."""
+    return world * sites_per_rank * steps / (max_seconds * 1e9)
+
+
+def cpu_baseline(sweeps: int = 4):
+    """The oracle, single-threaded, on the same lattice: `sweeps` sweeps
+    after creation (a bounded sample of the workload)."""
+    import oracle
+    o = oracle.Oracle(MODEL, DIM, L, Q, T, SEED)
+    o.sweep(1)
+    t0 = time.perf_counter()
+    o.sweep(sweeps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": N_SITES * sweeps / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} measured sweeps of the full L=256 lattice after 1 sweep from the "
+                      f"seeded start; {dt:.1f} s on one host core"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    # bounded sample: at most ~90 s of oracle sweeps in total
+    t0 = time.perf_counter()
+    probe = cpu_baseline(1)
+    per = N_SITES / (probe["value"] * 1e9)
+    steps = max(1, min(args.steps, int(90.0 / max(per, 1e-9))))
+    base = cpu_baseline(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * N_SITES / (base["value"] * 1e9),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    from paper_1403_7560_gb300 import build, sw
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    h = sw.sw_create(MODEL, DIM, L, Q, T, SEED + rank)
+    sw.sw_set_stream(h, stream.cuda_stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    sw.sw_discard(h, DISCARD)
+    for _ in range(max(args.warmup, 3)):
+        sw.sw_sweep(h, 1)
+        flush.fill_(1)
+    sw.sw_measure(h)
+    torch.cuda.synchronize()
+
+    # timed region: K measured sweeps, events around each, L2 flushed between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        sw.sw_sweep(h, 1)
+        ends[k].record(stream)
+        flush.fill_(k & 0xff)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    sw.sw_sync(h)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = allreduce_max(world, sum(step_ms) / 1e3)
+    value = aggregate(world, N_SITES, args.steps, total_s)
+    moments = sw.sw_measure(h)
+
+    # per-kernel durations: the same steps through the event-instrumented call
+    phase = np.zeros(4)
+    for k in range(args.steps):
+        phase += np.array(sw.sw_sweep_timed(h))
+        flush.fill_(k & 0xff)
+    torch.cuda.synchronize()
+    phase_ms = phase / args.steps
+    upd = []
+    for k in range(min(args.steps, 50)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sw.sw_discard(h, 1)
+        b.record(stream)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        upd.append(a.elapsed_time(b))
+    update_only = N_SITES / (statistics.mean(upd) * 1e6)
+
+    # end to end through the C ABI with pinned host buffers
+    host_in = torch.empty(N_SITES, dtype=torch.int8, pin_memory=True).numpy()
+    host_out = torch.empty(N_SITES, dtype=torch.int8, pin_memory=True).numpy()
+    sw.sw_get_spins(h, host_in)
+    e2e_steps = min(args.steps, 20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sw.sw_set_spins(h, host_in)          # H2D of the step's input state
+        sw.sw_sweep(h, 1)
+        sw.sw_get_spins(h, host_out)         # D2H of the new state (syncs)
+        m = sw.sw_measure(h)                 # D2H of the moments
+    e2e_s = allreduce_max(world, time.perf_counter() - t0)
+    e2e = {"value": aggregate(world, N_SITES, e2e_steps, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": N_SITES, "d2h_bytes_per_step": N_SITES + 10 * 8 + 6 * 8,
+           "steps": e2e_steps}
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        dom = int(np.argmax(phase_ms))
+        bps = KERNEL_BYTES_PER_SITE[PHASES[dom]] or 0.0
+        achieved = bps * N_SITES / (phase_ms[dom] * 1e-3) / 1e9
+        ms_per_step = 1e3 * total_s / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
+            "roofline": {"bound": "hbm", "kernel": PHASES[dom], "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "bytes_per_site": bps},
+            "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
+            "update_only": {"value": update_only, "unit": UNIT},
+            "b_ref": {"bytes_per_site": B_REF, "GBps": value * B_REF, "frac": value * B_REF / peak},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "e2e": e2e,
+            "moments": {"U": moments["U"], "e_per_spin": moments["e_per_spin"],
+                        "mean_cluster_size": moments["mean_cluster_size"]},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_sweeps)
+        print(json.dumps(line), flush=True)
+    sw.sw_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

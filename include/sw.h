@@ -1,0 +1,190 @@
+/*
+ * sw.h - C ABI of the GB300 Swendsen-Wang engine.
+ *
+ * One SW sweep (Komura & Okabe, Sec. 2) = (1) active bond generation,
+ * (2) cluster labeling, (3) cluster flip, followed by the measurement of the
+ * magnetization and energy (Sec. 2, equations for M and the Potts M^2; the
+ * moment ratio U of Sec. 3).  Models: Ising (Eq. for H_Ising), q-state Potts
+ * (Eq. for H_Potts) and classical XY (Eq. for H_XY) on the 2D square and 3D
+ * simple cubic lattices with periodic boundaries (Sec. 1).  Every step runs
+ * in CUDA kernels for sm_103a on one GPU; the host only launches them.
+ *
+ * Conventions shared by every call:
+ *   - N = L^dim sites; site i = x + L*(y + L*z), x fastest; J = 1.
+ *   - Spins (host or device buffers passed to the get/set calls):
+ *       SW_ISING  int8_t  +1 / -1
+ *       SW_POTTS  uint8_t 0 .. q-1
+ *       SW_XY     float   angle theta in [0, 2 pi)
+ *   - Bond bit-planes: plane d (0 <= d < dim) holds bond (i, i + e_d); each
+ *     row (fixed y, z) is padded to W = ceil(L/32) uint32 words; the bit of
+ *     site i is word d*R*W + row*W + (x >> 5), bit (x & 31), with
+ *     R = L^(dim-1) rows and row = y + L*z.
+ *   - Labels: int32, label[i] = smallest site index in i's cluster.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *     key = (seed low 32 bits, seed high 32 bits) and counter
+ *     (site, sweep, purpose, 0); sweep k (1-based) of the run uses k, the
+ *     initial state uses 0.  Purposes: 0 initial state (word 0); 1 bonds
+ *     (word d decides bond (i,d), word dim is the cluster draw of a root
+ *     i); 3 XY mirror angle (site 0, word 0).
+ *   - Ownership: the handle owns every device buffer it allocates; host
+ *     buffers passed in stay owned by the caller and are only read or
+ *     written during the call (the call synchronises the handle's stream).
+ *   - Errors: functions returning int return SW_OK (0) or a negative
+ *     sw_status; sw_create returns NULL.  sw_last_error() gives a message
+ *     for the last failure on the calling thread.  No C++ exception crosses
+ *     this interface.
+ *   - Streams: all GPU work of a handle is ordered on one CUDA stream (its
+ *     own non-blocking stream unless sw_set_stream gave another).  sw_sweep
+ *     and sw_discard only enqueue; the calls that return data synchronise.
+ */
+#ifndef SW_GB300_H
+#define SW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum sw_model { SW_ISING = 0, SW_POTTS = 1, SW_XY = 2 };
+
+enum sw_status {
+  SW_OK = 0,
+  SW_ERR_BAD_ARG = -1,  /* invalid argument, size or NULL handle          */
+  SW_ERR_OOM = -2,      /* device or host allocation failed                */
+  SW_ERR_CUDA = -3,     /* a CUDA call or kernel launch failed             */
+  SW_ERR_TIMEOUT = -4,  /* a device-side loop hit its iteration cap        */
+  SW_ERR_RANGE = -5     /* requested sweep records are no longer retained  */
+};
+
+typedef struct sw_handle sw_handle;
+
+/* Sums over the measured sweeps since the previous sw_measure (Sec. 2,
+ * outputs of the sample program; Sec. 3, moment ratio U).
+ *   M2 per sweep: Ising M^2 with M = sum s_i; Potts (q sum_k n_k^2 - N^2)/(q-1)
+ *   (Sec. 2, Potts equation); XY (sum cos)^2 + (sum sin)^2.  M4 = (M2)^2.
+ *   E per sweep: Ising -sum s_i s_j; Potts sum (1 - delta); XY
+ *   -sum cos(theta_i - theta_j).
+ *   U = <M4>/<M2>^2;  e_per_spin = <E>/N;  c_per_spin = (<E^2>-<E>^2)/(N T^2);
+ *   mean_cluster_size = N / <number of clusters>. */
+typedef struct sw_moments {
+  double n_sweeps;
+  double sum_M2;
+  double sum_M4;
+  double sum_E;
+  double sum_E2;
+  double sum_nclusters;
+  double U;
+  double e_per_spin;
+  double c_per_spin;
+  double mean_cluster_size;
+} sw_moments;
+
+/* One measured sweep's record (the per-sweep series).  Ising: M, E; Potts:
+ * E, S2 = sum_k n_k^2; XY: mx, my, e_xy.  M2 and Ed are the per-sweep M2 and
+ * E used by the accumulators. */
+typedef struct sw_record {
+  uint64_t sweep;
+  int64_t M;
+  int64_t E;
+  int64_t nclusters;
+  int64_t S2;
+  double mx;
+  double my;
+  double e_xy;
+  double M2;
+  double Ed;
+} sw_record;
+
+/* Create a lattice (paper: device_function_spinset + the parameters nx,
+ * mcs1/mcs2 of Sec. 2).  model: sw_model; dim: 2 or 3; L >= 4; q: Potts
+ * states 2..256 (ignored otherwise); T > 0 in units of J; seed: Philox key.
+ * The initial state is random from the seed (sweep counter 0).  Returns NULL
+ * on a bad argument, an oversized lattice (N * 2^b must fit in 32 bits, b =
+ * bits of the cluster draw: 1 for Ising/XY, ceil(log2 q) for Potts) or a
+ * CUDA failure.  Uses the current CUDA device. */
+sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed);
+
+/* Free every device buffer and the owned stream.  NULL is allowed. */
+void sw_destroy(sw_handle* h);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* sw_last_error(void);
+
+/* Enqueue n measured SW sweeps (Sec. 2 steps (1)-(3) + measurement): per
+ * sweep the records and the accumulators of sw_measure are updated on the
+ * device.  n >= 0.  Asynchronous: returns after the launches. */
+int sw_sweep(sw_handle* h, int n);
+
+/* Enqueue n SW sweeps without measurement (the paper's discarded mcs1
+ * sweeps; also the "update only" timing of Tables 1 and 2). */
+int sw_discard(sw_handle* h, int n);
+
+/* Synchronise, copy the accumulators of the sweeps measured since the last
+ * call into *out, then reset them.  Returns SW_ERR_TIMEOUT if any device
+ * loop of the queued sweeps hit its cap. */
+int sw_measure(sw_handle* h, sw_moments* out);
+
+/* Synchronise the handle's stream and report any device error flag. */
+int sw_sync(sw_handle* h);
+
+/* Use `stream` (a cudaStream_t, e.g. torch.cuda.Stream.cuda_stream; NULL =
+ * the legacy default stream) for all further work of the handle.  The
+ * caller keeps ownership of the stream and must keep it alive while the
+ * handle uses it. */
+int sw_set_stream(sw_handle* h, void* stream);
+
+/* Number of sweeps done so far (the sweep field of the Philox counter of
+ * the last sweep), and its setter for checkpoint/resume. */
+uint64_t sw_sweep_counter(sw_handle* h);
+int sw_set_sweep_counter(sw_handle* h, uint64_t k);
+
+/* Sizes of the buffers below: sites, bytes of the spin array, bond words. */
+size_t sw_num_sites(sw_handle* h);
+size_t sw_spin_bytes(sw_handle* h);
+size_t sw_bond_words(sw_handle* h);
+
+/* Copy the spin state to / from a caller-owned HOST buffer of exactly
+ * sw_spin_bytes bytes.  Synchronous. */
+int sw_get_spins(sw_handle* h, void* host, size_t bytes);
+int sw_set_spins(sw_handle* h, const void* host, size_t bytes);
+
+/* Same with a caller-owned DEVICE buffer; enqueued on the handle's stream
+ * (asynchronous with respect to the host). */
+int sw_get_spins_device(sw_handle* h, void* dev, size_t bytes);
+int sw_set_spins_device(sw_handle* h, const void* dev, size_t bytes);
+
+/* Canonical labels (min site index per cluster, Sec. 2 step (2)) of the
+ * clusters of the last sweep, into a host int32 buffer of n = N entries
+ * (all zero before the first sweep). */
+int sw_get_labels(sw_handle* h, int32_t* host, size_t n);
+
+/* Bond bit-planes of the last sweep into a host buffer of sw_bond_words
+ * words. */
+int sw_get_bonds(sw_handle* h, uint32_t* host, size_t words);
+
+/* Label the clusters of an injected bond mask (host bit-planes, layout
+ * above) with the same kernels the sweep uses, writing N canonical labels
+ * to host_labels.  Overwrites the handle's bond and label buffers (the
+ * spins are untouched).  For parity tests of the labeling step. */
+int sw_label_from_bonds(sw_handle* h, const uint32_t* host_mask, int32_t* host_labels);
+
+/* One measured sweep, like sw_sweep(h, 1), with CUDA events recorded on
+ * the handle's stream between its kernels.  Synchronises, then writes the
+ * device time of each phase in milliseconds to phase_ms[0..3]:
+ * [0] bonds + tile labels, [1] tile-boundary merge, [2] flip, [3]
+ * measurement.  nphase must be >= 4.  For profiling. */
+int sw_sweep_timed(sw_handle* h, float* phase_ms, int nphase);
+
+/* Records of measured sweeps first .. first+count-1 into a host array.  The
+ * handle retains the records of the last sw_series_capacity() measured
+ * sweeps; SW_ERR_RANGE if a requested one is gone or was not measured. */
+int sw_get_series(sw_handle* h, uint64_t first, size_t count, sw_record* host);
+size_t sw_series_capacity(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SW_GB300_H */

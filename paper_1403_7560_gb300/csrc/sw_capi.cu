@@ -1,0 +1,366 @@
+// C ABI of the SW engine (include/sw.h): handle life cycle, argument
+// validation, the sweep schedule on the handle's stream, and the debug /
+// integration getters.  All SW arithmetic runs in sw_kernels.cu; the host
+// computes only the per-run constants (bond threshold, 2/T) in sw_create.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sw.h"
+#include "sw_internal.h"
+
+using swgb::Lattice;
+using swgb::Measure;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kSeriesCap = 4096;
+
+}  // namespace
+
+struct sw_handle {
+  int model = 0, dim = 0, L = 0, q = 2;
+  double T = 0.0;
+  uint64_t seed = 0;
+  uint64_t sweep = 0;
+  size_t spin_bytes = 0, bond_words = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Lattice lat{};
+  Measure meas{};
+  int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
+  void* d_block = nullptr;      // one allocation holding every small buffer
+};
+
+namespace {
+
+// Bond probability (Sec. 2, step (1), sign restored): Ising
+// p = 1 - exp(-2/T); Potts (H = -sum(delta - 1)) p = 1 - exp(-1/T).  The
+// kernel tests draw < t with t = floor(p 2^32), p = -expm1(-a) in double.
+uint32_t bond_threshold(int model, double T) {
+  const double a = (model == SW_ISING) ? 2.0 / T : 1.0 / T;
+  double t = std::floor(-std::expm1(-a) * 4294967296.0);
+  if (t > 4294967295.0) t = 4294967295.0;
+  if (t < 0.0) t = 0.0;
+  return (uint32_t)t;
+}
+
+int draw_bits(int model, int q) {
+  if (model != SW_POTTS) return 1;
+  int b = 0;
+  while ((1 << b) < q) ++b;
+  return b;
+}
+
+void release(sw_handle* h) {
+  if (!h) return;
+  cudaFree(h->lat.spins);
+  cudaFree(h->lat.planes);
+  cudaFree(h->lat.forest);
+  cudaFree(h->d_labels);
+  cudaFree(h->d_block);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int check_device_error(sw_handle* h) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, h->lat.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  if (flag != 0) {
+    cudaMemsetAsync(h->lat.err, 0, sizeof(int), h->stream);
+    return fail(flag, "a device loop hit its iteration cap");
+  }
+  return SW_OK;
+}
+
+int run_sweeps(sw_handle* h, int n, bool measure) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  if (n < 0) return fail(SW_ERR_BAD_ARG, "n < 0");
+  for (int s = 0; s < n; ++s) {
+    if (h->sweep >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+    const uint32_t k = (uint32_t)(++h->sweep);
+    cudaError_t e = swgb::launch_bond_label(h->lat, h->model, k, false, h->stream);
+    if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
+    if (e == cudaSuccess)
+      e = swgb::launch_flip(h->lat, h->model, k, measure ? h->meas.nclusters : nullptr, h->stream);
+    if (e == cudaSuccess && measure) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+  }
+  return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sw_last_error(void) { return g_last_error.c_str(); }
+
+size_t sw_series_capacity(void) { return kSeriesCap; }
+
+sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) {
+  g_last_error.clear();
+  if (model < SW_ISING || model > SW_XY) { fail(SW_ERR_BAD_ARG, "model must be 0 (Ising), 1 (Potts) or 2 (XY)"); return nullptr; }
+  if (dim != 2 && dim != 3) { fail(SW_ERR_BAD_ARG, "dim must be 2 or 3"); return nullptr; }
+  if (L < 4) { fail(SW_ERR_BAD_ARG, "L must be >= 4"); return nullptr; }
+  if (!(T > 0.0) || !std::isfinite(T)) { fail(SW_ERR_BAD_ARG, "T must be finite and > 0"); return nullptr; }
+  if (model == SW_POTTS && (q < 2 || q > 256)) { fail(SW_ERR_BAD_ARG, "Potts q must be in 2..256"); return nullptr; }
+  if (model != SW_POTTS) q = 2;
+  const int sb = draw_bits(model, q);
+  const double Nd = std::pow((double)L, dim);
+  if (Nd * std::ldexp(1.0, sb) > 4294967296.0) {
+    fail(SW_ERR_BAD_ARG, "lattice too large: N * 2^drawbits must fit in 32 bits");
+    return nullptr;
+  }
+  const uint32_t N = (uint32_t)Nd;
+
+  sw_handle* h = new (std::nothrow) sw_handle();
+  if (!h) { fail(SW_ERR_OOM, "host allocation"); return nullptr; }
+  h->model = model; h->dim = dim; h->L = L; h->q = q; h->T = T; h->seed = seed;
+  h->spin_bytes = (size_t)N * (model == SW_XY ? sizeof(float) : 1);
+
+  Lattice& lat = h->lat;
+  lat.N = N; lat.L = L; lat.dim = dim; lat.W = (L + 31) / 32;
+  lat.R = (uint32_t)(N / (uint32_t)L);
+  swgb::tiles_for(dim, L, &lat.ntx, &lat.nty, &lat.ntz);
+  lat.q = q; lat.sbits = sb;
+  lat.t_bond = (model == SW_XY) ? 0u : bond_threshold(model, T);
+  lat.twoK = (float)(2.0 / T);
+  lat.key0 = (uint32_t)(seed & 0xffffffffu);
+  lat.key1 = (uint32_t)(seed >> 32);
+  h->bond_words = (size_t)dim * lat.R * (size_t)lat.W;
+
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { cuda_fail(e, "stream"); release(h); return nullptr; }
+  h->own_stream = true;
+
+  // small buffers, carved from one block: err, ticket, nclusters, acc,
+  // hist, partials, series ring
+  const size_t off_err = 0, off_ticket = 16, off_ncl = 32, off_acc = 64;
+  const size_t off_hist = off_acc + 64;
+  const size_t off_pi = off_hist + 256 * 8;
+  const size_t off_pd = off_pi + 2 * 8 * (size_t)swgb::kMeasureBlocks;
+  const size_t off_series = off_pd + 3 * 8 * (size_t)swgb::kMeasureBlocks;
+  const size_t block_bytes = off_series + sizeof(swgb::Record) * (size_t)kSeriesCap;
+
+  if ((e = cudaMalloc(&lat.spins, h->spin_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&lat.planes, h->bond_words * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&lat.forest, (size_t)N * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_block, block_bytes)) != cudaSuccess) {
+    fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,
+         std::string("device allocation: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    release(h);
+    return nullptr;
+  }
+  char* blk = static_cast<char*>(h->d_block);
+  lat.err = reinterpret_cast<int*>(blk + off_err);
+  h->meas.ticket = reinterpret_cast<unsigned int*>(blk + off_ticket);
+  h->meas.nclusters = reinterpret_cast<unsigned long long*>(blk + off_ncl);
+  h->meas.acc = reinterpret_cast<double*>(blk + off_acc);
+  h->meas.hist = reinterpret_cast<unsigned long long*>(blk + off_hist);
+  h->meas.part_i = reinterpret_cast<long long*>(blk + off_pi);
+  h->meas.part_d = reinterpret_cast<double*>(blk + off_pd);
+  h->meas.series = blk + off_series;
+  h->meas.series_cap = kSeriesCap;
+
+  if ((e = cudaMemsetAsync(h->d_block, 0, block_bytes, h->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(blk + off_series, 0xff, block_bytes - off_series, h->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(lat.planes, 0, h->bond_words * 4, h->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(lat.forest, 0, (size_t)N * 4, h->stream)) != cudaSuccess ||
+      (e = swgb::launch_init(lat, model, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+    cuda_fail(e, "init");
+    release(h);
+    return nullptr;
+  }
+  return h;
+}
+
+void sw_destroy(sw_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  release(h);
+}
+
+int sw_sweep(sw_handle* h, int n) { return run_sweeps(h, n, true); }
+
+int sw_sweep_timed(sw_handle* h, float* phase_ms, int nphase) {
+  if (!h || !phase_ms) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (nphase < 4) return fail(SW_ERR_BAD_ARG, "nphase < 4");
+  if (h->sweep >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+  cudaEvent_t ev[5];
+  int made = 0;
+  cudaError_t e = cudaSuccess;
+  for (; made < 5 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  if (e != cudaSuccess) {
+    for (int k = 0; k < made - 1; ++k) cudaEventDestroy(ev[k]);
+    return cuda_fail(e, "event");
+  }
+  const uint32_t k = (uint32_t)(++h->sweep);
+  e = cudaEventRecord(ev[0], h->stream);
+  if (e == cudaSuccess) e = swgb::launch_bond_label(h->lat, h->model, k, false, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+  if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+  if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas.nclusters, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+  if (e == cudaSuccess) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+  for (int p = 0; p < 4 && e == cudaSuccess; ++p) e = cudaEventElapsedTime(&phase_ms[p], ev[p], ev[p + 1]);
+  for (int p = 0; p < 5; ++p) cudaEventDestroy(ev[p]);
+  if (e != cudaSuccess) return cuda_fail(e, "timed sweep");
+  return check_device_error(h);
+}
+
+int sw_discard(sw_handle* h, int n) { return run_sweeps(h, n, false); }
+
+int sw_sync(sw_handle* h) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  return check_device_error(h);
+}
+
+int sw_measure(sw_handle* h, sw_moments* out) {
+  if (!h || !out) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  double acc[6];
+  cudaError_t e = cudaMemcpyAsync(acc, h->meas.acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->meas.acc, 0, sizeof(acc), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "measure copy");
+  const int rc = check_device_error(h);
+  if (rc != SW_OK) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->n_sweeps = acc[0];
+  out->sum_M2 = acc[1];
+  out->sum_M4 = acc[2];
+  out->sum_E = acc[3];
+  out->sum_E2 = acc[4];
+  out->sum_nclusters = acc[5];
+  if (acc[0] > 0) {
+    const double n = acc[0], N = (double)h->lat.N;
+    const double m2 = acc[1] / n, m4 = acc[2] / n, e1 = acc[3] / n, e2 = acc[4] / n;
+    out->U = m2 > 0 ? m4 / (m2 * m2) : 0.0;
+    out->e_per_spin = e1 / N;
+    out->c_per_spin = (e2 - e1 * e1) / (N * h->T * h->T);
+    out->mean_cluster_size = acc[5] > 0 ? N / (acc[5] / n) : 0.0;
+  }
+  return SW_OK;
+}
+
+int sw_set_stream(sw_handle* h, void* stream) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  h->own_stream = false;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return SW_OK;
+}
+
+uint64_t sw_sweep_counter(sw_handle* h) { return h ? h->sweep : 0; }
+
+int sw_set_sweep_counter(sw_handle* h, uint64_t k) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  if (k >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter must be < 2^32 - 1");
+  h->sweep = k;
+  return SW_OK;
+}
+
+size_t sw_num_sites(sw_handle* h) { return h ? h->lat.N : 0; }
+size_t sw_spin_bytes(sw_handle* h) { return h ? h->spin_bytes : 0; }
+size_t sw_bond_words(sw_handle* h) { return h ? h->bond_words : 0; }
+
+int sw_get_spins(sw_handle* h, void* host, size_t bytes) {
+  if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
+  cudaError_t e = cudaMemcpyAsync(host, h->lat.spins, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_spins");
+  return check_device_error(h);
+}
+
+int sw_set_spins(sw_handle* h, const void* host, size_t bytes) {
+  if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
+  cudaError_t e = cudaMemcpyAsync(h->lat.spins, host, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_spins");
+  return check_device_error(h);
+}
+
+int sw_get_spins_device(sw_handle* h, void* dev, size_t bytes) {
+  if (!h || !dev) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
+  cudaError_t e = cudaMemcpyAsync(dev, h->lat.spins, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  return e == cudaSuccess ? SW_OK : cuda_fail(e, "get_spins_device");
+}
+
+int sw_set_spins_device(sw_handle* h, const void* dev, size_t bytes) {
+  if (!h || !dev) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
+  cudaError_t e = cudaMemcpyAsync(h->lat.spins, dev, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  return e == cudaSuccess ? SW_OK : cuda_fail(e, "set_spins_device");
+}
+
+int sw_get_labels(sw_handle* h, int32_t* host, size_t n) {
+  if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (n != h->lat.N) return fail(SW_ERR_BAD_ARG, "n != number of sites");
+  cudaError_t e = cudaSuccess;
+  if (!h->d_labels) e = cudaMalloc(&h->d_labels, (size_t)h->lat.N * 4);
+  if (e != cudaSuccess) return cuda_fail(e, "labels buffer");
+  if ((e = swgb::launch_labels_out(h->lat, h->d_labels, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(host, h->d_labels, n * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "get_labels");
+  return check_device_error(h);
+}
+
+int sw_get_bonds(sw_handle* h, uint32_t* host, size_t words) {
+  if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (words != h->bond_words) return fail(SW_ERR_BAD_ARG, "words != sw_bond_words");
+  cudaError_t e = cudaMemcpyAsync(host, h->lat.planes, words * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_bonds");
+  return check_device_error(h);
+}
+
+int sw_label_from_bonds(sw_handle* h, const uint32_t* host_mask, int32_t* host_labels) {
+  if (!h || !host_mask || !host_labels) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpyAsync(h->lat.planes, host_mask, h->bond_words * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = swgb::launch_bond_label(h->lat, h->model, 0u, true, h->stream);
+  if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "label_from_bonds");
+  return sw_get_labels(h, host_labels, h->lat.N);
+}
+
+int sw_get_series(sw_handle* h, uint64_t first, size_t count, sw_record* host) {
+  if (!h || (!host && count)) return fail(SW_ERR_BAD_ARG, "NULL argument");
+  if (count > (size_t)kSeriesCap) return fail(SW_ERR_RANGE, "count exceeds the retained series");
+  const int rc = check_device_error(h);
+  if (rc != SW_OK) return rc;
+  static_assert(sizeof(swgb::Record) == sizeof(sw_record), "record layout");
+  if (count == 0) return SW_OK;
+  std::vector<sw_record> ring(kSeriesCap);
+  cudaError_t e = cudaMemcpy(ring.data(), h->meas.series, sizeof(sw_record) * kSeriesCap,
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "get_series");
+  for (size_t k = 0; k < count; ++k) {
+    const uint64_t s = first + k;
+    host[k] = ring[s % kSeriesCap];
+    if (host[k].sweep != s) return fail(SW_ERR_RANGE, "sweep record not retained or not measured");
+  }
+  return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Internal interface between the C-ABI layer (sw_capi.cu) and the kernels
+// (sw_kernels.cu).  Not installed; the public interface is include/sw.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swgb {
+
+enum Model { kIsing = 0, kPotts = 1, kXY = 2 };
+
+// Device-side view of one lattice, passed by value to every kernel.
+struct Lattice {
+  void* spins;          // int8 (Ising), uint8 (Potts) or float (XY), N entries
+  uint32_t* planes;     // bond bit-planes, dim * R * W words
+  uint32_t* forest;     // per site: (parent << sbits) | cluster draw
+  int* err;             // device error flag (0 = ok, else an sw_status)
+  uint32_t N;           // L^dim
+  int L, dim, W;        // W = words per lattice row
+  uint32_t R;           // rows = L^(dim-1)
+  int ntx, nty, ntz;    // tiles per axis
+  int q, sbits;         // Potts states; bits of the cluster draw
+  uint32_t t_bond;      // Ising/Potts: bond active iff draw < t_bond
+  float twoK;           // XY: 2/T as float
+  uint32_t key0, key1;  // Philox key = seed
+};
+
+// Buffers of the moment reduction (the per-sweep record and accumulators).
+struct Measure {
+  unsigned long long* nclusters;  // roots counted by the flip kernel
+  unsigned long long* hist;       // Potts histogram [q]
+  long long* part_i;              // per-block integer partials [2 * nblk]
+  double* part_d;                 // per-block float partials [3 * nblk]
+  unsigned int* ticket;           // blocks finished (last-block pattern)
+  double* acc;                    // n, sum M2, M4, E, E2, nclusters
+  void* series;                   // sw_record ring
+  int series_cap;
+};
+
+// Record layout written by the measurement kernel (mirrors sw_record).
+struct Record {
+  unsigned long long sweep;
+  long long M, E, nclusters, S2;
+  double mx, my, e_xy, M2, Ed;
+};
+
+constexpr int kMeasureBlocks = 1216;  // 152 SMs x 8 blocks of 256 threads
+constexpr int kFlipBlocks = 1216;
+
+// Tile shape of the labeling kernels (x extent is always one 32-bit word).
+constexpr int kTileY2 = 64;  // 2D: 32 x 64 sites
+constexpr int kTileY3 = 8;   // 3D: 32 x 8 x 8 sites
+constexpr int kTileZ3 = 8;
+
+void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
+
+cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
+cudaError_t launch_bond_label(const Lattice& lat, int model, uint32_t sweep, bool from_mask,
+                              cudaStream_t st);
+cudaError_t launch_merge(const Lattice& lat, cudaStream_t st);
+cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep,
+                        unsigned long long* nclusters, cudaStream_t st);
+cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const Measure& m,
+                           cudaStream_t st);
+cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);
+
+}  // namespace swgb

@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the C ABI in include/sw.h (same names, argument
+marshalling only).  Every step of the sweep runs in the CUDA library
+libsw_gb300.so; if that library is missing this module raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SW_ISING, SW_POTTS, SW_XY = 0, 1, 2
+SW_OK, SW_ERR_BAD_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_RANGE = 0, -1, -2, -3, -4, -5
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sw error {code}: {msg}")
+        self.code = code
+
+
+class sw_moments(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "n_sweeps", "sum_M2", "sum_M4", "sum_E", "sum_E2", "sum_nclusters",
+        "U", "e_per_spin", "c_per_spin", "mean_cluster_size")]
+
+
+class sw_record(ctypes.Structure):
+    _fields_ = [("sweep", ctypes.c_uint64), ("M", ctypes.c_int64), ("E", ctypes.c_int64),
+                ("nclusters", ctypes.c_int64), ("S2", ctypes.c_int64),
+                ("mx", ctypes.c_double), ("my", ctypes.c_double), ("e_xy", ctypes.c_double),
+                ("M2", ctypes.c_double), ("Ed", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); the full exported surface of include/sw.h
+_vp, _sz, _u64, _i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+_SIGNATURES = {
+    "sw_create": (_vp, [_i, _i, _i, _i, ctypes.c_double, _u64]),
+    "sw_destroy": (None, [_vp]),
+    "sw_last_error": (ctypes.c_char_p, []),
+    "sw_sweep": (_i, [_vp, _i]),
+    "sw_discard": (_i, [_vp, _i]),
+    "sw_measure": (_i, [_vp, ctypes.POINTER(sw_moments)]),
+    "sw_sync": (_i, [_vp]),
+    "sw_set_stream": (_i, [_vp, _vp]),
+    "sw_sweep_counter": (_u64, [_vp]),
+    "sw_set_sweep_counter": (_i, [_vp, _u64]),
+    "sw_num_sites": (_sz, [_vp]),
+    "sw_spin_bytes": (_sz, [_vp]),
+    "sw_bond_words": (_sz, [_vp]),
+    "sw_get_spins": (_i, [_vp, _vp, _sz]),
+    "sw_set_spins": (_i, [_vp, _vp, _sz]),
+    "sw_get_spins_device": (_i, [_vp, _vp, _sz]),
+    "sw_set_spins_device": (_i, [_vp, _vp, _sz]),
+    "sw_get_labels": (_i, [_vp, _vp, _sz]),
+    "sw_get_bonds": (_i, [_vp, _vp, _sz]),
+    "sw_label_from_bonds": (_i, [_vp, _vp, _vp]),
+    "sw_get_series": (_i, [_vp, _u64, _sz, ctypes.POINTER(sw_record)]),
+    "sw_series_capacity": (_sz, []),
+    "sw_sweep_timed": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libsw_gb300.so (build it first with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() first")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def sw_last_error() -> str:
+    return lib().sw_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != SW_OK:
+        raise SwError(rc, sw_last_error())
+
+
+def spin_dtype(model: int):
+    return {SW_ISING: np.int8, SW_POTTS: np.uint8, SW_XY: np.float32}[model]
+
+
+class Handle:
+    """An sw_handle* plus the arguments it was created with."""
+
+    def __init__(self, ptr: int, model: int, dim: int, L: int, q: int, T: float, seed: int):
+        self.ptr, self.model, self.dim, self.L, self.q, self.T, self.seed = ptr, model, dim, L, q, T, seed
+        self.N = L ** dim
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.ptr)
+
+
+def sw_create(model: int, dim: int, L: int, q: int, T: float, seed: int) -> Handle:
+    ptr = lib().sw_create(model, dim, L, q, T, seed)
+    if not ptr:
+        raise SwError(SW_ERR_BAD_ARG, sw_last_error())
+    return Handle(ptr, model, dim, L, q, T, seed)
+
+
+def sw_destroy(h: Handle):
+    if h is not None and h.ptr:
+        lib().sw_destroy(h)
+        h.ptr = 0
+
+
+def sw_sweep(h: Handle, n: int):
+    _check(lib().sw_sweep(h, n))
+
+
+def sw_discard(h: Handle, n: int):
+    _check(lib().sw_discard(h, n))
+
+
+def sw_measure(h: Handle) -> dict:
+    m = sw_moments()
+    _check(lib().sw_measure(h, ctypes.byref(m)))
+    return {f: getattr(m, f) for f, _ in sw_moments._fields_}
+
+
+def sw_sync(h: Handle):
+    _check(lib().sw_sync(h))
+
+
+def sw_set_stream(h: Handle, stream: int):
+    _check(lib().sw_set_stream(h, ctypes.c_void_p(stream)))
+
+
+def sw_sweep_counter(h: Handle) -> int:
+    return int(lib().sw_sweep_counter(h))
+
+
+def sw_set_sweep_counter(h: Handle, k: int):
+    _check(lib().sw_set_sweep_counter(h, k))
+
+
+def sw_num_sites(h: Handle) -> int:
+    return int(lib().sw_num_sites(h))
+
+
+def sw_spin_bytes(h: Handle) -> int:
+    return int(lib().sw_spin_bytes(h))
+
+
+def sw_bond_words(h: Handle) -> int:
+    return int(lib().sw_bond_words(h))
+
+
+def sw_get_spins(h: Handle, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty(h.N, dtype=spin_dtype(h.model))
+    _check(lib().sw_get_spins(h, out.ctypes.data, out.nbytes))
+    return out
+
+
+def sw_set_spins(h: Handle, spins: np.ndarray):
+    s = np.ascontiguousarray(spins, dtype=spin_dtype(h.model))
+    _check(lib().sw_set_spins(h, s.ctypes.data, s.nbytes))
+
+
+def sw_get_spins_device(h: Handle, dev_ptr: int, nbytes: int):
+    _check(lib().sw_get_spins_device(h, ctypes.c_void_p(dev_ptr), nbytes))
+
+
+def sw_set_spins_device(h: Handle, dev_ptr: int, nbytes: int):
+    _check(lib().sw_set_spins_device(h, ctypes.c_void_p(dev_ptr), nbytes))
+
+
+def sw_get_labels(h: Handle) -> np.ndarray:
+    out = np.empty(h.N, dtype=np.int32)
+    _check(lib().sw_get_labels(h, out.ctypes.data, out.size))
+    return out
+
+
+def sw_get_bonds(h: Handle) -> np.ndarray:
+    out = np.empty(sw_bond_words(h), dtype=np.uint32)
+    _check(lib().sw_get_bonds(h, out.ctypes.data, out.size))
+    return out
+
+
+def sw_label_from_bonds(h: Handle, mask: np.ndarray) -> np.ndarray:
+    m = np.ascontiguousarray(mask, dtype=np.uint32)
+    if m.size != sw_bond_words(h):
+        raise SwError(SW_ERR_BAD_ARG, "mask size != sw_bond_words")
+    out = np.empty(h.N, dtype=np.int32)
+    _check(lib().sw_label_from_bonds(h, m.ctypes.data, out.ctypes.data))
+    return out
+
+
+def sw_get_series(h: Handle, first: int, count: int) -> list[dict]:
+    arr = (sw_record * max(count, 1))()
+    _check(lib().sw_get_series(h, first, count, arr))
+    return [{f: getattr(arr[k], f) for f, _ in sw_record._fields_} for k in range(count)]
+
+
+def sw_sweep_timed(h: Handle) -> list[float]:
+    """One measured sweep; device milliseconds of [bonds+tile labels, merge,
+    flip, measurement]."""
+    out = (ctypes.c_float * 4)()
+    _check(lib().sw_sweep_timed(h, out, 4))
+    return [float(v) for v in out]
+
+
+def sw_series_capacity() -> int:
+    return int(lib().sw_series_capacity())

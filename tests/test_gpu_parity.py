@@ -1,0 +1,329 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Ising and Potts: initial state, bond planes, labels, spins, per-sweep records
+and FP64 accumulators must be bit-identical to the oracle sweep by sweep.
+XY: bonds may differ only where the float bond test is within rounding of
+its threshold; labels are bit-identical given the GPU's mask; angles agree
+within 1e-5 rad; per-sweep moments within the float summation bound.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from oracle import ISING, POTTS, XY
+
+pytestmark = pytest.mark.gpu
+
+ANGLE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_7560_gb300 import build, sw as swmod
+    build.build()
+    return swmod
+
+
+def record_key(model):
+    return ("M", "E", "nclusters") if model == ISING else ("E", "S2", "nclusters")
+
+
+def run_exact_parity(sw, model, dim, L, q, T, seed, sweeps, check_labels=True):
+    h = sw.sw_create(model, dim, L, q, T, seed)
+    o = oracle.Oracle(model, dim, L, q, T, seed)
+    try:
+        assert np.array_equal(sw.sw_get_spins(h), o.spins), "initial state"
+        for k in range(1, sweeps + 1):
+            sw.sw_sweep(h, 1)
+            o.sweep(1)
+            assert np.array_equal(sw.sw_get_bonds(h), o.planes), f"bonds, sweep {k}"
+            if check_labels:
+                assert np.array_equal(sw.sw_get_labels(h), o.labels), f"labels, sweep {k}"
+            assert np.array_equal(sw.sw_get_spins(h), o.spins), f"spins, sweep {k}"
+            rec = sw.sw_get_series(h, k, 1)[0]
+            ref = o.last_record()
+            for f in record_key(model) + ("M2", "Ed"):
+                assert rec[f] == ref[f], (f, k, rec[f], ref[f])
+        got, ref = sw.sw_measure(h), o.take_acc()
+        for f in ("n_sweeps", "sum_M2", "sum_M4", "sum_E", "sum_E2", "sum_nclusters"):
+            assert got[f] == ref[f], (f, got[f], ref[f])
+    finally:
+        sw.sw_destroy(h)
+        o.close()
+
+
+@pytest.mark.parametrize("model,dim,L,q", [
+    (ISING, 2, 4, 2), (ISING, 2, 48, 2), (ISING, 3, 5, 2), (ISING, 3, 40, 2),
+    (POTTS, 2, 33, 3), (POTTS, 3, 17, 4), (POTTS, 2, 16, 256), (XY, 2, 20, 2), (XY, 3, 9, 2)])
+def test_initial_state(sw, model, dim, L, q):
+    h = sw.sw_create(model, dim, L, q, 1.0, 77)
+    try:
+        assert np.array_equal(sw.sw_get_spins(h), oracle.init_spins(model, dim, L, q, 77))
+    finally:
+        sw.sw_destroy(h)
+
+
+@pytest.mark.parametrize("dim,L,T", [
+    (2, 4, 2.269185), (2, 16, 2.269185), (2, 31, 2.0), (2, 48, 2.269185), (2, 64, 2.269185),
+    (2, 100, 2.4), (2, 130, 1.8), (3, 4, 4.5), (3, 8, 4.5115), (3, 9, 4.0), (3, 33, 4.5115),
+    (3, 40, 5.0), (3, 64, 4.5115)])
+def test_ising_sweeps_bit_exact(sw, dim, L, T):
+    run_exact_parity(sw, ISING, dim, L, 2, T, seed=1000 + L, sweeps=12)
+
+
+@pytest.mark.parametrize("dim,L,q,T", [
+    (2, 64, 3, 0.994973), (2, 48, 4, 0.910239), (2, 37, 8, 0.74), (2, 32, 256, 0.3),
+    (3, 16, 3, 1.8), (3, 24, 8, 1.3)])
+def test_potts_sweeps_bit_exact(sw, dim, L, q, T):
+    run_exact_parity(sw, POTTS, dim, L, q, T, seed=2000 + L, sweeps=12)
+
+
+def test_low_and_high_temperature_limits(sw):
+    # T -> 0: one cluster per equal-spin domain; T -> infinity: no bonds
+    run_exact_parity(sw, ISING, 2, 40, 2, 1e-3, seed=5, sweeps=4)
+    run_exact_parity(sw, ISING, 3, 12, 2, 1e-3, seed=6, sweeps=4)
+    run_exact_parity(sw, POTTS, 2, 40, 5, 1e6, seed=7, sweeps=3)
+
+
+def test_config_2d_ising_L64_full_run(sw):
+    """2D Ising L=64 at T=2.269185, 200 discarded + 1000 measured sweeps:
+    every measured record and the accumulators equal the oracle's."""
+    model, dim, L, q, T, seed, ndisc, nmeas = inputs.WORKLOADS["ising2d_L64"]
+    h = sw.sw_create(model, dim, L, q, T, seed)
+    o = oracle.Oracle(model, dim, L, q, T, seed)
+    try:
+        sw.sw_discard(h, ndisc)
+        o.sweep(ndisc, measure=False)
+        sw.sw_measure(h)
+        o.take_acc()
+        recs = []
+        for _ in range(nmeas):
+            o.sweep(1)
+            recs.append(o.last_record())
+        sw.sw_sweep(h, nmeas)
+        got = sw.sw_get_series(h, ndisc + 1, nmeas)
+        for k, (g, r) in enumerate(zip(got, recs)):
+            assert (g["M"], g["E"], g["nclusters"]) == (r["M"], r["E"], r["nclusters"]), k
+        a, b = sw.sw_measure(h), o.take_acc()
+        for f in ("n_sweeps", "sum_M2", "sum_M4", "sum_E", "sum_E2", "sum_nclusters"):
+            assert a[f] == b[f], f
+        assert np.array_equal(sw.sw_get_spins(h), o.spins)
+        assert np.array_equal(sw.sw_get_labels(h), o.labels)
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_config_3d_ising_L256_first_sweeps(sw):
+    """3D Ising L=256 at K=0.2216546 in the benchmark's launch configuration:
+    the first sweeps are bit-identical to the oracle (spins, labels, bonds,
+    records)."""
+    model, dim, L, q, T, seed, _, _ = inputs.WORKLOADS["ising3d_L256"]
+    run_exact_parity(sw, model, dim, L, q, T, seed, sweeps=2)
+
+
+# ---------------------------------------------------------------- labels
+@pytest.mark.parametrize("dim,L", [(2, 4), (2, 31), (2, 64), (2, 97), (2, 200), (3, 4), (3, 8),
+                                   (3, 13), (3, 32), (3, 41)])
+@pytest.mark.parametrize("density", [0.3, 0.5, 0.7, 0.95])
+def test_labels_random_masks(sw, dim, L, density):
+    h = sw.sw_create(ISING, dim, L, 2, 2.0, 1)
+    try:
+        m = inputs.random_mask(dim, L, density, seed=L * 7 + int(100 * density))
+        assert np.array_equal(sw.sw_label_from_bonds(h, m), oracle.labels(dim, L, m))
+    finally:
+        sw.sw_destroy(h)
+
+
+@pytest.mark.parametrize("dim,L", [(2, 4), (2, 48), (2, 96), (3, 5), (3, 24), (3, 33)])
+def test_labels_structured_masks(sw, dim, L):
+    h = sw.sw_create(ISING, dim, L, 2, 2.0, 1)
+    N = L ** dim
+    try:
+        on = inputs.pack_planes(np.ones((dim, N), bool), dim, L)
+        assert (sw.sw_label_from_bonds(h, on) == 0).all()
+        off = inputs.pack_planes(np.zeros((dim, N), bool), dim, L)
+        assert np.array_equal(sw.sw_label_from_bonds(h, off), np.arange(N))
+        for axis in range(dim):
+            m = inputs.stripe_mask(dim, L, axis)
+            assert np.array_equal(sw.sw_label_from_bonds(h, m), oracle.labels(dim, L, m))
+        if dim == 2:
+            m = inputs.spiral_mask(L)
+            assert (sw.sw_label_from_bonds(h, m) == 0).all()
+    finally:
+        sw.sw_destroy(h)
+
+
+# ---------------------------------------------------------------- XY
+def ang_diff(a, b):
+    d = np.abs(a.astype(np.float64) - b.astype(np.float64)) % (2 * np.pi)
+    return np.minimum(d, 2 * np.pi - d)
+
+
+def xy_borderline(model_T, dim, L, seed, k, theta, gpu_mask, ora_mask):
+    """Every bond where GPU and oracle disagree must have its uniform draw
+    within float rounding of the bond probability."""
+    diff = inputs.unpack_planes(gpu_mask ^ ora_mask, dim, L)
+    if not diff.any():
+        return 0
+    phi = float(oracle.xy_phi(seed, k))
+    th = theta.astype(np.float64)
+    x = np.cos(th - phi)
+    n = 0
+    for d in range(dim):
+        idx = np.nonzero(diff[d])[0]
+        if idx.size == 0:
+            continue
+        from exact import neighbours
+        j = neighbours(dim, L, d)[idx]
+        prod = x[idx] * x[j]
+        p = np.where(prod > 0, -np.expm1(-2.0 / model_T * prod), 0.0)
+        w = np.array([oracle.philox([int(i), k, 1, 0], [seed & 0xffffffff, seed >> 32])[d] for i in idx])
+        u = (w >> 8).astype(np.float64) * 2.0 ** -24
+        assert np.all(np.abs(u - p) < 1e-5) or np.all(np.abs(prod) < 1e-5), (u, p, prod)
+        n += idx.size
+    return n
+
+
+@pytest.mark.parametrize("dim,L,T,sweeps", [(2, 64, 0.89, 8), (3, 32, 2.2, 6), (3, 48, 2.0, 4),
+                                            (2, 37, 1.1, 6)])
+def test_xy_sweeps(sw, dim, L, T, sweeps):
+    seed = 3000 + L
+    h = sw.sw_create(XY, dim, L, 2, T, seed)
+    N = L ** dim
+    try:
+        theta = sw.sw_get_spins(h)
+        assert np.array_equal(theta, oracle.init_spins(XY, dim, L, 2, seed))
+        mismatches = 0
+        for k in range(1, sweeps + 1):
+            sw.sw_sweep(h, 1)
+            gmask = sw.sw_get_bonds(h)
+            glab = sw.sw_get_labels(h)
+            gnew = sw.sw_get_spins(h)
+            omask = oracle.bonds(XY, dim, L, 2, T, seed, k, theta)
+            mismatches += xy_borderline(T, dim, L, seed, k, theta, gmask, omask)
+            assert np.array_equal(glab, oracle.labels(dim, L, gmask)), k
+            onew, ncl = oracle.flip(XY, dim, L, 2, seed, k, glab, theta)
+            assert ang_diff(gnew, onew).max() < ANGLE_TOL, k
+            rec = sw.sw_get_series(h, k, 1)[0]
+            ref = oracle.moments(XY, dim, L, 2, gnew)
+            tol = 2e-6 * N * (dim + 1) + 1e-3
+            assert abs(rec["mx"] - ref["mx"]) < tol and abs(rec["my"] - ref["my"]) < tol
+            assert abs(rec["e_xy"] - ref["e_xy"]) < tol
+            assert rec["nclusters"] == ncl
+            theta = gnew
+        assert mismatches <= max(2, N * dim * sweeps // 100000)
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_xy_config_3d_L256_one_sweep(sw):
+    model, dim, L, q, T, seed, _, _ = inputs.WORKLOADS["xy3d_L256"]
+    h = sw.sw_create(model, dim, L, q, T, seed)
+    try:
+        theta = sw.sw_get_spins(h)
+        sw.sw_sweep(h, 1)
+        gmask = sw.sw_get_bonds(h)
+        glab = sw.sw_get_labels(h)
+        gnew = sw.sw_get_spins(h)
+        omask = oracle.bonds(XY, dim, L, 2, T, seed, 1, theta)
+        diff = int(np.unpackbits((gmask ^ omask).view(np.uint8)).sum())
+        assert diff <= 200
+        assert np.array_equal(glab, oracle.labels(dim, L, gmask))
+        onew, _ = oracle.flip(XY, dim, L, 2, seed, 1, glab, theta)
+        assert ang_diff(gnew, onew).max() < ANGLE_TOL
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_xy_ensemble_moments_within_3_sigma(sw):
+    """Independent GPU and oracle XY runs (2D L=16, T=0.9): binned means of
+    E and M^2 agree within 3 combined standard errors (plus 1% slack)."""
+    dim, L, T = 2, 16, 0.9
+    bins, per = 20, 2000
+
+    def binned(step_measure):
+        rows = []
+        for _ in range(bins):
+            a = step_measure()
+            rows.append([a["sum_E"] / a["n_sweeps"], a["sum_M2"] / a["n_sweeps"]])
+        r = np.array(rows)
+        return r.mean(0), r.std(0, ddof=1) / math.sqrt(bins)
+
+    h = sw.sw_create(XY, dim, L, 2, T, 4242)
+    o = oracle.Oracle(XY, dim, L, 2, T, 4243)
+    try:
+        sw.sw_discard(h, 500)
+        o.sweep(500, measure=False)
+        sw.sw_measure(h)
+        o.take_acc()
+
+        def g():
+            sw.sw_sweep(h, per)
+            return sw.sw_measure(h)
+
+        def c():
+            o.sweep(per)
+            return o.take_acc()
+        gm, ge = binned(g)
+        cm, ce = binned(c)
+        for j in range(2):
+            assert abs(gm[j] - cm[j]) < 3 * math.hypot(ge[j], ce[j]) + 0.01 * abs(cm[j]), (j, gm, cm, ge, ce)
+    finally:
+        sw.sw_destroy(h)
+
+
+# ---------------------------------------------------------------- API behaviour
+def test_resume_is_exact(sw):
+    a = sw.sw_create(POTTS, 3, 20, 3, 1.7, 91)
+    b = sw.sw_create(POTTS, 3, 20, 3, 1.7, 91)
+    try:
+        sw.sw_sweep(a, 9)
+        sw.sw_set_spins(b, sw.sw_get_spins(a))
+        sw.sw_set_sweep_counter(b, sw.sw_sweep_counter(a))
+        sw.sw_sweep(a, 6)
+        sw.sw_sweep(b, 6)
+        assert np.array_equal(sw.sw_get_spins(a), sw.sw_get_spins(b))
+    finally:
+        sw.sw_destroy(a)
+        sw.sw_destroy(b)
+
+
+def test_user_stream_and_device_buffers(sw):
+    import torch
+    h = sw.sw_create(ISING, 3, 32, 2, 4.5, 12)
+    try:
+        st = torch.cuda.Stream()
+        sw.sw_set_stream(h, st.cuda_stream)
+        buf = torch.empty(32 ** 3, dtype=torch.int8, device="cuda")
+        sw.sw_sweep(h, 3)
+        sw.sw_get_spins_device(h, buf.data_ptr(), buf.numel())
+        st.synchronize()
+        assert np.array_equal(buf.cpu().numpy(), sw.sw_get_spins(h))
+        flipped = (-buf).contiguous()
+        sw.sw_set_spins_device(h, flipped.data_ptr(), flipped.numel())
+        st.synchronize()
+        assert np.array_equal(sw.sw_get_spins(h), flipped.cpu().numpy())
+    finally:
+        sw.sw_destroy(h)
+
+
+def test_series_range_errors(sw):
+    h = sw.sw_create(ISING, 2, 16, 2, 2.0, 1)
+    try:
+        sw.sw_discard(h, 3)
+        sw.sw_sweep(h, 2)
+        with pytest.raises(sw.SwError):
+            sw.sw_get_series(h, 1, 1)          # discarded sweep: no record
+        assert [r["sweep"] for r in sw.sw_get_series(h, 4, 2)] == [4, 5]
+        with pytest.raises(sw.SwError):
+            sw.sw_get_series(h, 6, 1)          # not done yet
+    finally:
+        sw.sw_destroy(h)
