@@ -183,6 +183,40 @@ int sw_sweep_timed(sw_handle* h, float* phase_ms, int nphase);
 int sw_get_series(sw_handle* h, uint64_t first, size_t count, sw_record* host);
 size_t sw_series_capacity(void);
 
+/* ------------------------------------------------------------------------
+ * Labeling without device allocation.  The paper has no counterpart: this
+ * serves callers that may not allocate device memory themselves, such as a
+ * plugin inside a host framework that owns every device byte through its
+ * own pool, or a latency-critical loop where cudaMalloc / cudaFree would
+ * synchronise the device and stall other streams.
+ *
+ * Computes exactly what sw_label_from_bonds computes (canonical min-index
+ * labels of the clusters of a bond mask in the bit-plane layout above, with
+ * the same kernels), but takes DEVICE buffers from the caller and allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library call.  Its working
+ * memory (the union-find forest and an error flag) is one static device
+ * array of SW_NOALLOC_MAX_SITES + 64 words (8 MiB + 256 B) in this library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ *   dim, L       2 or 3, L >= 4, and L^dim <= SW_NOALLOC_MAX_SITES; larger
+ *                lattices are rejected with SW_ERR_BAD_ARG before any GPU work
+ *   dev_mask     device pointer, bond bit-planes (read only)
+ *   dev_labels   device pointer, L^dim int32 labels (written)
+ *   stream       cudaStream_t to run on (NULL = legacy default stream)
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on a device shares the same array and leaves
+ * its contents behind; the call clears the error flag itself, and the forest
+ * needs no clearing.  Calls whose GPU work overlaps (on different streams or
+ * from different threads) race on the array and must be serialised by the
+ * caller.  The call synchronises `stream` before returning and reports a
+ * device loop that hit its cap as SW_ERR_TIMEOUT; sw_last_error() gives the
+ * message of a failure. */
+#define SW_NOALLOC_MAX_SITES (1u << 21)
+int sw_label_from_bonds_noalloc(int dim, int L, const uint32_t* dev_mask, int32_t* dev_labels,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

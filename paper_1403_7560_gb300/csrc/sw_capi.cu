@@ -16,8 +16,12 @@ using swgb::Lattice;
 using swgb::Measure;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+void swgb::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
 
 int fail(int code, const std::string& msg) {
   g_last_error = msg;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace swgb {
 
 enum Model { kIsing = 0, kPotts = 1, kXY = 2 };
@@ -53,6 +55,9 @@ constexpr int kTileY3 = 8;   // 3D: 32 x 8 x 8 sites
 constexpr int kTileZ3 = 8;
 
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
+
+// Message returned by sw_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
 cudaError_t launch_bond_label(const Lattice& lat, int model, uint32_t sweep, bool from_mask,

@@ -65,7 +65,10 @@ _SIGNATURES = {
     "sw_get_series": (_i, [_vp, _u64, _sz, ctypes.POINTER(sw_record)]),
     "sw_series_capacity": (_sz, []),
     "sw_sweep_timed": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
+    "sw_label_from_bonds_noalloc": (_i, [_i, _i, _vp, _vp, _vp]),
 }
+
+SW_NOALLOC_MAX_SITES = 1 << 21
 
 
 def library_path() -> str:
@@ -222,6 +225,14 @@ def sw_sweep_timed(h: Handle) -> list[float]:
     out = (ctypes.c_float * 4)()
     _check(lib().sw_sweep_timed(h, out, 4))
     return [float(v) for v in out]
+
+
+def sw_label_from_bonds_noalloc(dim: int, L: int, dev_mask: int, dev_labels: int, stream: int = 0):
+    """Labels of a device bond mask into a device int32 buffer, using the
+    library's fixed scratch array instead of any allocation (pointers are
+    device addresses, e.g. torch tensor data_ptr())."""
+    _check(lib().sw_label_from_bonds_noalloc(dim, L, ctypes.c_void_p(dev_mask),
+                                             ctypes.c_void_p(dev_labels), ctypes.c_void_p(stream)))
 
 
 def sw_series_capacity() -> int:
