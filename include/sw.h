@@ -22,10 +22,17 @@
  *   - Labels: int32, label[i] = smallest site index in i's cluster.
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
  *     key = (seed low 32 bits, seed high 32 bits) and counter
- *     (site, sweep, purpose, 0); sweep k (1-based) of the run uses k, the
- *     initial state uses 0.  Purposes: 0 initial state (word 0); 1 bonds
- *     (word d decides bond (i,d), word dim is the cluster draw of a root
- *     i); 3 XY mirror angle (site 0, word 0).
+ *     (c0, sweep, purpose, c3); sweep k (1-based) of the run uses k, the
+ *     initial state uses 0.  Purposes:
+ *       0 initial state: counter (i, 0, 0, 0), word 0;
+ *       1 bonds: Ising/Potts bond (i,d) is active iff the spins are equal
+ *         and a 32-bit uniform u(i,d) < floor(p 2^32); bit 31-k of u(i,d)
+ *         is bit (x & 31) of word k of the sequence of i's row word
+ *         g = row*W + (x >> 5), word k = word (k & 3) of counter
+ *         (g, k_sweep, 1, 8d + k/4).  XY: counter (i, sweep, 1, 0), word d;
+ *       2 cluster draws: counter (i >> 2, sweep, 2, 0), word (i & 3) is
+ *         the draw w of site i, used when i is the root of its cluster;
+ *       3 XY mirror angle: counter (0, sweep, 3, 0), word 0.
  *   - Ownership: the handle owns every device buffer it allocates; host
  *     buffers passed in stay owned by the caller and are only read or
  *     written during the call (the call synchronises the handle's stream).
@@ -101,9 +108,9 @@ typedef struct sw_record {
  * mcs1/mcs2 of Sec. 2).  model: sw_model; dim: 2 or 3; L >= 4; q: Potts
  * states 2..256 (ignored otherwise); T > 0 in units of J; seed: Philox key.
  * The initial state is random from the seed (sweep counter 0).  Returns NULL
- * on a bad argument, an oversized lattice (N * 2^b must fit in 32 bits, b =
- * bits of the cluster draw: 1 for Ising/XY, ceil(log2 q) for Potts) or a
- * CUDA failure.  Uses the current CUDA device. */
+ * on a bad argument, an oversized lattice (N * 2^(b+1) must fit in 32 bits,
+ * b = bits of the cluster draw: 1 for Ising/XY, ceil(log2 q) for Potts) or
+ * a CUDA failure.  Uses the current CUDA device. */
 sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed);
 
 /* Free every device buffer and the owned stream.  NULL is allowed. */

@@ -27,12 +27,20 @@
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11), key = (seed low, seed high),
- * counter = (site, sweep, purpose, 0).  The paper uses an LCG and says any
- * other generator may be used (Sec. 2, technical remarks).
- *   purpose 0 (INIT): initial state, word 0
- *   purpose 1 (BOND): words 0..D-1 decide bonds (i,d); word D is site i's
- *                     cluster draw, used when i is the root of its cluster
- *   purpose 3 (AXIS): counter (0, sweep, 3, 0), word 0 -> XY mirror angle
+ * 32-bit counter words (c0, c1 = sweep, c2 = purpose, c3).  The paper uses
+ * an LCG and says any other generator may be used (Sec. 2, technical
+ * remarks).
+ *   purpose 0 (INIT):  counter (i, 0, 0, 0), word 0 -> initial state of i.
+ *   purpose 1 (BOND):  Ising/Potts: the 32-bit uniform u(i,d) of bond (i,d)
+ *                      is spread over a sequence of 32 words shared by the
+ *                      32 sites of i's row word g = row*W + (x>>5): bit 31-k
+ *                      of u(i,d) is bit (x & 31) of the k-th word, the k-th
+ *                      word being word (k & 3) of counter (g, k, 1, 8d + k/4).
+ *                      XY: counter (i, k, 1, 0), word d -> u(i,d).
+ *   purpose 2 (DRAW):  counter (i >> 2, k, 2, 0), word (i & 3) -> the
+ *                      cluster draw w(i), used when i is a cluster root.
+ *   purpose 3 (AXIS):  counter (0, k, 3, 0), word 0 -> XY mirror angle.
+ * (k is the sweep number, starting at 1; the initial state uses 0.)
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,6 +53,7 @@
 
 #define PURPOSE_INIT 0u
 #define PURPOSE_BOND 1u
+#define PURPOSE_DRAW 2u
 #define PURPOSE_AXIS 3u
 
 /* ------------------------------------------------------------------------ */
@@ -79,9 +88,9 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-static void draw4(uint64_t seed, uint32_t site, uint32_t sweep, uint32_t purpose,
+static void draw4(uint64_t seed, uint32_t c0, uint32_t sweep, uint32_t purpose, uint32_t c3,
                   uint32_t w[4]) {
-  uint32_t ctr[4] = {site, sweep, purpose, 0u};
+  uint32_t ctr[4] = {c0, sweep, purpose, c3};
   uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
   oracle_philox4x32_10(ctr, key, w);
 }
@@ -142,7 +151,7 @@ uint32_t oracle_bond_threshold(int model, double T) {
  * shared by all sites): phi = (w0 >> 8) * (2 pi / 2^24), taken in float. */
 float oracle_xy_phi(uint64_t seed, uint32_t sweep) {
   uint32_t w[4];
-  draw4(seed, 0u, sweep, PURPOSE_AXIS, w);
+  draw4(seed, 0u, sweep, PURPOSE_AXIS, 0u, w);
   const float step = (float)(6.283185307179586476925 / 16777216.0);
   return (float)(w[0] >> 8) * step;
 }
@@ -155,7 +164,7 @@ int oracle_init(int model, int dim, int L, int q, uint64_t seed, void* spins) {
   const float step = (float)(6.283185307179586476925 / 16777216.0);
   for (int64_t i = 0; i < N; ++i) {
     uint32_t w[4];
-    draw4(seed, (uint32_t)i, 0u, PURPOSE_INIT, w);
+    draw4(seed, (uint32_t)i, 0u, PURPOSE_INIT, 0u, w);
     if (model == OR_ISING) {
       ((int8_t*)spins)[i] = (w[0] >> 31) ? (int8_t)-1 : (int8_t)1;
     } else if (model == OR_POTTS) {
@@ -168,8 +177,26 @@ int oracle_init(int model, int dim, int L, int q, uint64_t seed, void* spins) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* The 32 words of the bond sequence of row word g and direction d: word k
+ * is word (k & 3) of counter (g, sweep, 1, 8d + k/4). */
+static void bond_sequence(uint64_t seed, uint32_t sweep, uint32_t g, int d, uint32_t R[32]) {
+  for (int c = 0; c < 8; ++c) {
+    uint32_t w[4];
+    draw4(seed, g, sweep, PURPOSE_BOND, (uint32_t)(8 * d + c), w);
+    for (int j = 0; j < 4; ++j) R[4 * c + j] = w[j];
+  }
+}
+
+/* u(i,d) of the site at bit b of the row word: bit 31-k of u is bit b of
+ * the k-th word of the sequence. */
+static uint32_t bond_uniform(const uint32_t R[32], int b) {
+  uint32_t u = 0;
+  for (int k = 0; k < 32; ++k) u |= ((R[k] >> b) & 1u) << (31 - k);
+  return u;
+}
+
 /* Step (1): active bond generation (Sec. 2).
- * Ising/Potts: bond (i,j) active iff s_i == s_j and u_d < t.
+ * Ising/Potts: bond (i,j) active iff s_i == s_j and u(i,d) < t.
  * XY (embedded Ising clusters, Wolff 1989; Sec. 1 and Sec. 2 remarks on the
  * clock model): project on r = (cos phi, sin phi): x_i = cos(theta_i - phi);
  * bond active iff x_i x_j > 0 and u < 1 - exp(-2K x_i x_j), with
@@ -182,16 +209,27 @@ void oracle_bonds(int model, int dim, int L, int q, double T, uint64_t seed,
   uint32_t t = (model == OR_XY) ? 0u : oracle_bond_threshold(model, T);
   float phi = (model == OR_XY) ? oracle_xy_phi(seed, sweep) : 0.0f;
   float twoK = (float)(2.0 / T);
+  uint32_t R[3][32];           /* bond sequences of the current row word */
+  int64_t cached_g = -1;
   for (int64_t i = 0; i < N; ++i) {
+    int64_t x = i % L;
+    int64_t g = (i / L) * row_words(L) + (x >> 5);
     uint32_t w[4];
-    draw4(seed, (uint32_t)i, sweep, PURPOSE_BOND, w);
+    if (model == OR_XY) {
+      draw4(seed, (uint32_t)i, sweep, PURPOSE_BOND, 0u, w);
+    } else if (g != cached_g) {
+      for (int d = 0; d < dim; ++d) bond_sequence(seed, sweep, (uint32_t)g, d, R[d]);
+      cached_g = g;
+    }
     for (int d = 0; d < dim; ++d) {
       int64_t j = neighbour(dim, L, i, d);
       int active = 0;
       if (model == OR_ISING) {
-        active = (((const int8_t*)spins)[i] == ((const int8_t*)spins)[j]) && (w[d] < t);
+        active = (((const int8_t*)spins)[i] == ((const int8_t*)spins)[j]) &&
+                 (bond_uniform(R[d], (int)(x & 31)) < t);
       } else if (model == OR_POTTS) {
-        active = (((const uint8_t*)spins)[i] == ((const uint8_t*)spins)[j]) && (w[d] < t);
+        active = (((const uint8_t*)spins)[i] == ((const uint8_t*)spins)[j]) &&
+                 (bond_uniform(R[d], (int)(x & 31)) < t);
       } else {
         float ti = ((const float*)spins)[i];
         float tj = ((const float*)spins)[j];
@@ -204,7 +242,7 @@ void oracle_bonds(int model, int dim, int L, int q, double T, uint64_t seed,
           active = u < p;
         }
       }
-      if (active) planes[plane_word_index(dim, L, i, d)] |= 1u << ((i % L) & 31);
+      if (active) planes[plane_word_index(dim, L, i, d)] |= 1u << (x & 31);
     }
   }
 }
@@ -246,7 +284,7 @@ int oracle_labels(int dim, int L, const uint32_t* planes, int32_t* labels) {
 
 /* ------------------------------------------------------------------------ */
 /* Step (3): spin flip (Sec. 2; paper: spin_select then spin_flip).  Each
- * cluster takes one new state, drawn from word D of its root's BOND draw:
+ * cluster takes one new state from its root's cluster draw w (purpose 2):
  *   Ising: +1 if w < 2^31 else -1   (set at random, Sec. 2 step (3))
  *   Potts: floor(w q / 2^32)        (uniform of q states)
  *   XY:    reflect about the line perpendicular to r iff w >= 2^31:
@@ -262,8 +300,8 @@ int64_t oracle_flip(int model, int dim, int L, int q, uint64_t seed, uint32_t sw
   for (int64_t r = 0; r < N; ++r) {
     if (labels[r] != r) continue;
     uint32_t w[4];
-    draw4(seed, (uint32_t)r, sweep, PURPOSE_BOND, w);
-    root_draw[r] = w[dim];
+    draw4(seed, (uint32_t)(r >> 2), sweep, PURPOSE_DRAW, 0u, w);
+    root_draw[r] = w[r & 3];
     ++nclusters;
   }
   double phi = (model == OR_XY) ? (double)oracle_xy_phi(seed, sweep) : 0.0;

@@ -93,13 +93,24 @@ int check_device_error(sw_handle* h) {
   return SW_OK;
 }
 
+// Step (1) and the tile half of step (2): Ising/Potts bonds are drawn inside
+// the labeling kernel; XY bonds come from their own kernel first.
+cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k) {
+  if (h->model == SW_XY) {
+    cudaError_t e = swgb::launch_bonds_xy(h->lat, k, h->stream);
+    if (e != cudaSuccess) return e;
+    return swgb::launch_label(h->lat, k, true, h->stream);
+  }
+  return swgb::launch_label(h->lat, k, false, h->stream);
+}
+
 int run_sweeps(sw_handle* h, int n, bool measure) {
   if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
   if (n < 0) return fail(SW_ERR_BAD_ARG, "n < 0");
   for (int s = 0; s < n; ++s) {
     if (h->sweep >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
     const uint32_t k = (uint32_t)(++h->sweep);
-    cudaError_t e = swgb::launch_bond_label(h->lat, h->model, k, false, h->stream);
+    cudaError_t e = launch_bonds_labels(h, k);
     if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
     if (e == cudaSuccess)
       e = swgb::launch_flip(h->lat, h->model, k, measure ? h->meas.nclusters : nullptr, h->stream);
@@ -127,8 +138,8 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   if (model != SW_POTTS) q = 2;
   const int sb = draw_bits(model, q);
   const double Nd = std::pow((double)L, dim);
-  if (Nd * std::ldexp(1.0, sb) > 4294967296.0) {
-    fail(SW_ERR_BAD_ARG, "lattice too large: N * 2^drawbits must fit in 32 bits");
+  if (Nd * std::ldexp(1.0, sb + 1) > 4294967296.0) {
+    fail(SW_ERR_BAD_ARG, "lattice too large: N * 2^(drawbits+1) must fit in 32 bits");
     return nullptr;
   }
   const uint32_t N = (uint32_t)Nd;
@@ -218,7 +229,7 @@ int sw_sweep_timed(sw_handle* h, float* phase_ms, int nphase) {
   }
   const uint32_t k = (uint32_t)(++h->sweep);
   e = cudaEventRecord(ev[0], h->stream);
-  if (e == cudaSuccess) e = swgb::launch_bond_label(h->lat, h->model, k, false, h->stream);
+  if (e == cudaSuccess) e = launch_bonds_labels(h, k);
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
   if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
@@ -342,7 +353,7 @@ int sw_get_bonds(sw_handle* h, uint32_t* host, size_t words) {
 int sw_label_from_bonds(sw_handle* h, const uint32_t* host_mask, int32_t* host_labels) {
   if (!h || !host_mask || !host_labels) return fail(SW_ERR_BAD_ARG, "NULL argument");
   cudaError_t e = cudaMemcpyAsync(h->lat.planes, host_mask, h->bond_words * 4, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = swgb::launch_bond_label(h->lat, h->model, 0u, true, h->stream);
+  if (e == cudaSuccess) e = swgb::launch_label(h->lat, 0u, true, h->stream);
   if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "label_from_bonds");
   return sw_get_labels(h, host_labels, h->lat.N);

@@ -1,0 +1,235 @@
+// Device helpers shared by the SW kernels: Philox4x32-10, the bit-sliced
+// Bernoulli word, byte-lane comparisons, tile geometry, union-find in shared
+// and global memory, and warp/block reductions.
+#pragma once
+
+#include "sw_internal.h"
+
+namespace swgb {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kErrTimeout = -4;
+
+// Philox purposes (third counter word).
+constexpr uint32_t kInit = 0u, kBond = 1u, kDraw = 2u, kAxis = 3u;
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds; per round two 32x32
+// multiplications whose high words are xor-ed with the other counter words
+// and the round key, key bumped by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& w, int j) {
+  return j == 0 ? w.x : j == 1 ? w.y : j == 2 ? w.z : w.w;
+}
+
+// XY mirror direction of a sweep: phi = (w0 >> 8) * fl(2 pi)/2^24 in float.
+__device__ __forceinline__ float xy_phi(const Lattice& lat, uint32_t sweep) {
+  const uint4 w = philox(0u, sweep, kAxis, 0u, lat.key0, lat.key1);
+  return __fmul_rn((float)(w.x >> 8), 0x1.921fb6p-22f);
+}
+
+// One step of the bit-sliced comparison u < t, most significant bit first:
+// r holds bit `hb` of the 32 lanes' uniforms.
+__device__ __forceinline__ void cmp_step(uint32_t& lt, uint32_t& eq, uint32_t r, uint32_t t, int hb) {
+  if ((t >> hb) & 1u) {
+    lt |= eq & ~r;
+    eq &= r;
+  } else {
+    eq &= ~r;
+  }
+}
+
+// Bernoulli word of row word g, direction d: bit b is set iff the 32-bit
+// uniform u(b) < t, where bit 31-k of u(b) is bit b of the k-th word of the
+// sequence, word k = word (k & 3) of Philox(g, sweep, BOND, 8d + k/4).  The
+// comparison stops once every lane is decided; undecided lanes after 32
+// bits have u == t and stay 0.
+__device__ __forceinline__ uint32_t bernoulli_word(uint32_t g, uint32_t sweep, int d, uint32_t t,
+                                                   uint32_t k0, uint32_t k1) {
+  uint32_t lt = 0u, eq = kFull;
+#pragma unroll 1
+  for (int c = 0; c < 8; ++c) {
+    const uint4 w = philox(g, sweep, kBond, (uint32_t)(8 * d + c), k0, k1);
+    const int hb = 31 - 4 * c;
+    cmp_step(lt, eq, w.x, t, hb);
+    cmp_step(lt, eq, w.y, t, hb - 1);
+    cmp_step(lt, eq, w.z, t, hb - 2);
+    cmp_step(lt, eq, w.w, t, hb - 3);
+    if (eq == 0u) break;
+  }
+  return lt;
+}
+
+// Cluster draw value of a site from its 32-bit draw word w: floor(w q / 2^32)
+// (Ising and XY use q = 2: 1 = flip to -1 / reflect).
+__device__ __forceinline__ uint32_t draw_value(uint32_t w, uint32_t q) {
+  return (uint32_t)(((unsigned long long)w * q) >> 32);
+}
+
+// 32 equality bits of two 32-byte rows held as 8 little-endian words.
+__device__ __forceinline__ uint32_t eq_bits(const uint32_t* a, const uint32_t* b) {
+  uint32_t m = 0u;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t e = __vcmpeq4(a[k], b[k]);
+    const uint32_t nib = ((e >> 7) & 1u) | ((e >> 14) & 2u) | ((e >> 21) & 4u) | ((e >> 28) & 8u);
+    m |= nib << (4 * k);
+  }
+  return m;
+}
+
+// Highest set bit of `starts` at or below bit b (the start of b's x-run).
+__device__ __forceinline__ uint32_t run_start(uint32_t starts, int b) {
+  return 31u - __clz(starts & (kFull >> (31 - b)));
+}
+
+// ---------------------------------------------------------------- tiles
+// A tile is 32 (one bit-plane word) x TY x TZ sites; one CTA of TY*TZ
+// threads labels it.
+template <int D>
+struct Tile;
+template <>
+struct Tile<2> {
+  static constexpr int TY = kTile2Y, TZ = 1, ROWS = TY * TZ;
+};
+template <>
+struct Tile<3> {
+  static constexpr int TY = kTile3Y, TZ = kTile3Z, ROWS = TY * TZ;
+};
+
+struct TileCoord {
+  int tx, x0, y0, z0;
+};
+
+template <int D>
+__device__ __forceinline__ TileCoord tile_coord(const Lattice& lat) {
+  int b = blockIdx.x;
+  TileCoord c;
+  c.tx = b % lat.ntx;
+  b /= lat.ntx;
+  c.x0 = c.tx * 32;
+  c.y0 = (b % lat.nty) * Tile<D>::TY;
+  c.z0 = (b / lat.nty) * Tile<D>::TZ;
+  return c;
+}
+
+// ---------------------------------------------------------------- union-find
+// Shared-memory forest of one tile: parents only decrease, so every loop is
+// bounded by the tile size; the caps only guard against corrupted input.
+__device__ __forceinline__ uint32_t sfind(volatile uint32_t* par, uint32_t x) {
+  for (int it = 0; it < 65536; ++it) {
+    const uint32_t p = par[x];
+    if (p == x) return x;
+    const uint32_t gp = par[p];
+    if (gp == p) return p;
+    par[x] = gp;  // path halving on a non-root
+    x = gp;
+  }
+  return x;
+}
+
+__device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b, int* err) {
+  volatile uint32_t* vp = par;
+  for (int it = 0; it < 65536; ++it) {
+    a = sfind(vp, a);
+    b = sfind(vp, b);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicMin(&par[a], b);
+    if (old == a) return;
+    a = old;
+  }
+  atomicExch(err, kErrTimeout);
+}
+
+// Global forest over tile-local roots: word = (parent << shift) | marker |
+// draw, shift = sb + 1, marker = 1 << sb set on every local root (the only
+// nodes these functions touch).  Links always point to a smaller index, so
+// the root of every tree is its smallest site index.
+__device__ __forceinline__ uint32_t gfind(uint32_t* f, uint32_t x, int shift, uint32_t marker) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    const uint32_t p = __ldcg(&f[x]) >> shift;
+    if (p == x) return x;
+    const uint32_t gp = __ldcg(&f[p]) >> shift;
+    if (gp == p) return p;
+    __stcg(&f[x], (gp << shift) | marker);  // path halving on a non-root
+    x = gp;
+  }
+  return x;
+}
+
+__device__ __forceinline__ void gunion(uint32_t* f, uint32_t a, uint32_t b, int sb, int* err) {
+  const int shift = sb + 1;
+  const uint32_t marker = 1u << sb;
+  for (int it = 0; it < (1 << 20); ++it) {
+    a = gfind(f, a, shift, marker);
+    b = gfind(f, b, shift, marker);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicMin(&f[a], (b << shift) | marker);
+    if ((old >> shift) == a) return;
+    a = old >> shift;
+  }
+  atomicExch(err, kErrTimeout);
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ long long warp_sum(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// Block total (fixed order) from each warp's total; valid in thread 0.
+template <int NW, typename T>
+__device__ __forceinline__ T block_combine(T warp_total, T* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[warp] = warp_total;
+  __syncthreads();
+  T r = T(0);
+  if (threadIdx.x < 32) {
+    r = (lane < NW) ? scratch[lane] : T(0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+}  // namespace dev
+}  // namespace swgb

@@ -1,5 +1,6 @@
-// Internal interface between the C-ABI layer (sw_capi.cu) and the kernels
-// (sw_kernels.cu).  Not installed; the public interface is include/sw.h.
+// Internal interface between the C-ABI layer (sw_capi.cu, sw_noalloc.cu) and
+// the kernels (sw_label.cu, sw_flip.cu, sw_measure.cu).  Not installed; the
+// public interface is include/sw.h.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -47,12 +48,13 @@ struct Record {
 };
 
 constexpr int kMeasureBlocks = 1216;  // 152 SMs x 8 blocks of 256 threads
-constexpr int kFlipBlocks = 1216;
 
-// Tile shape of the labeling kernels (x extent is always one 32-bit word).
-constexpr int kTileY2 = 64;  // 2D: 32 x 64 sites
-constexpr int kTileY3 = 8;   // 3D: 32 x 8 x 8 sites
-constexpr int kTileZ3 = 8;
+// Tile shape of the labeling, merge and flip kernels: 32 sites along x (one
+// bit-plane word) by TY (by TZ); one CTA of TY*TZ threads per tile.
+constexpr int kTile2Y = 256;  // 2D: 32 x 256 sites
+constexpr int kTile3Y = 16;   // 3D: 32 x 16 x 16 sites
+constexpr int kTile3Z = 16;
+constexpr int kTileThreads = 256;
 
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
 
@@ -60,8 +62,11 @@ void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
 void set_last_error(const std::string& msg);
 
 cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
-cudaError_t launch_bond_label(const Lattice& lat, int model, uint32_t sweep, bool from_mask,
-                              cudaStream_t st);
+// Bonds of the XY model (lane per site) into the bit-planes.
+cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, cudaStream_t st);
+// Tile labels (+ Ising/Potts bonds when from_mask is false; cluster draws
+// when sweep != 0) into the forest.
+cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st);
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st);
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep,
                         unsigned long long* nclusters, cudaStream_t st);

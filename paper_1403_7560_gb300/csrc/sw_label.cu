@@ -1,0 +1,288 @@
+// Steps (1) and (2) of the SW sweep (Komura & Okabe, Sec. 2): active bond
+// generation and the tile-local half of the cluster labeling.
+//
+// k_label: one CTA per 32 x TY (x TZ) tile, one thread per 32-site row word.
+//   phase 1 (thread per row word): Ising/Potts bonds from the int8/uint8
+//     spins -- equality of the row with its +x/+y/+z neighbour rows from
+//     byte-lane compares, AND a bit-sliced Bernoulli word per direction
+//     (u < t decided for 32 sites at once from whole Philox words) -- and
+//     the row's cluster draws; or the bonds read from the bit-planes.
+//   phase 2 (lane per site): every site's parent is the start of its x-run.
+//   phase 3 (thread per row word): one shared-memory union per pair of runs
+//     joined by +y / +z bonds inside the tile (runs already joined through
+//     the previous bit are skipped).
+//   phase 4 (lane per site): find the tile-local root and write the forest
+//     word (root as a global index, local-root marker, cluster draw).
+// k_bonds_xy: XY bonds (lane per site): project on the sweep's mirror axis
+//   and test the embedded-Ising probability; ballot into the bit-planes.
+#include "sw_device.cuh"
+
+namespace swgb {
+namespace {
+
+using namespace dev;
+
+// The 32 spin bytes of a row word and of its +x, +y, +z neighbour words.
+struct RowBytes {
+  uint32_t a[8], ax[8], ay[8], az[8];
+};
+
+template <int D>
+__device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint32_t row,
+                                          uint32_t row_y, uint32_t row_z, RowBytes& rb) {
+  const uint32_t base = row * (uint32_t)L + (uint32_t)x0;
+  if ((L & 31) == 0) {
+    // 32-byte aligned rows: two 16-byte loads per row word
+    const uint4* p = reinterpret_cast<const uint4*>(s + base);
+    const uint4* py = reinterpret_cast<const uint4*>(s + row_y * (uint32_t)L + (uint32_t)x0);
+    uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
+    rb.a[0] = v0.x; rb.a[1] = v0.y; rb.a[2] = v0.z; rb.a[3] = v0.w;
+    rb.a[4] = v1.x; rb.a[5] = v1.y; rb.a[6] = v1.z; rb.a[7] = v1.w;
+    v0 = __ldg(py); v1 = __ldg(py + 1);
+    rb.ay[0] = v0.x; rb.ay[1] = v0.y; rb.ay[2] = v0.z; rb.ay[3] = v0.w;
+    rb.ay[4] = v1.x; rb.ay[5] = v1.y; rb.ay[6] = v1.z; rb.ay[7] = v1.w;
+    if (D == 3) {
+      const uint4* pz = reinterpret_cast<const uint4*>(s + row_z * (uint32_t)L + (uint32_t)x0);
+      v0 = __ldg(pz); v1 = __ldg(pz + 1);
+      rb.az[0] = v0.x; rb.az[1] = v0.y; rb.az[2] = v0.z; rb.az[3] = v0.w;
+      rb.az[4] = v1.x; rb.az[5] = v1.y; rb.az[6] = v1.z; rb.az[7] = v1.w;
+    }
+    // +x neighbours: the row shifted by one byte; the last one wraps to x = 0
+    const uint32_t nx = (x0 + 32 < L) ? s[base + 32] : s[row * (uint32_t)L];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) rb.ax[k] = __byte_perm(rb.a[k], rb.a[k + 1], 0x4321);
+    rb.ax[7] = __byte_perm(rb.a[7], nx, 0x4321);
+  } else {
+    // general L: byte loads of the valid sites, zero elsewhere
+#pragma unroll
+    for (int k = 0; k < 8; ++k) rb.a[k] = rb.ax[k] = rb.ay[k] = rb.az[k] = 0u;
+    const uint32_t rowL = row * (uint32_t)L, rowyL = row_y * (uint32_t)L, rowzL = row_z * (uint32_t)L;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const int x = x0 + b;
+      if (x < L) {
+        const int x1 = (x + 1 == L) ? 0 : x + 1;
+        const int sh = 8 * (b & 3);
+        rb.a[b >> 2] |= (uint32_t)s[rowL + x] << sh;
+        rb.ax[b >> 2] |= (uint32_t)s[rowL + x1] << sh;
+        rb.ay[b >> 2] |= (uint32_t)s[rowyL + x] << sh;
+        if (D == 3) rb.az[b >> 2] |= (uint32_t)s[rowzL + x] << sh;
+      }
+    }
+  }
+}
+
+template <int D, bool FROM_MASK>
+__global__ void __launch_bounds__(kTileThreads) k_label(Lattice lat, uint32_t sweep) {
+  constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ, ROWS = Tile<D>::ROWS;
+  constexpr int NW = kTileThreads / 32, RPW = ROWS / NW;
+  static_assert(ROWS == kTileThreads, "one thread per row word");
+  __shared__ uint32_t par[ROWS * 32];
+  __shared__ uint8_t sdraw[ROWS * 32];
+  __shared__ uint32_t sX[ROWS], sS[ROWS];
+
+  const TileCoord tc = tile_coord<D>(lat);
+  const int L = lat.L;
+  const uint32_t plane = lat.R * (uint32_t)lat.W;
+  const int nvalid = min(32, L - tc.x0);
+  const uint32_t vmask = (nvalid >= 32) ? kFull : ((1u << nvalid) - 1u);
+  const bool draws = (sweep != 0u);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // ---- phase 1: bonds, runs and draws of this thread's row word
+  const int r = threadIdx.x;
+  const int ry = r % TY, rz = r / TY;
+  const int y = tc.y0 + ry, z = tc.z0 + rz;
+  const bool rowv = (y < L) && (D == 2 || z < L);
+  const int y1 = (y + 1 == L) ? 0 : y + 1;
+  const int z1 = (D == 3) ? ((z + 1 == L) ? 0 : z + 1) : 0;
+  uint32_t X = 0u, Y = 0u, Z = 0u, S = 0u, XW = 0u;
+  if (rowv) {
+    const uint32_t row = (uint32_t)y + (uint32_t)L * (uint32_t)z;
+    const uint32_t g = row * (uint32_t)lat.W + (uint32_t)tc.tx;
+    uint32_t A0, A1, A2 = 0u;
+    if (FROM_MASK) {
+      A0 = __ldg(&lat.planes[g]) & vmask;
+      A1 = __ldg(&lat.planes[plane + g]) & vmask;
+      if (D == 3) A2 = __ldg(&lat.planes[2 * plane + g]) & vmask;
+    } else {
+      RowBytes rb;
+      const uint32_t row_y = (uint32_t)y1 + (uint32_t)L * (uint32_t)z;
+      const uint32_t row_z = (uint32_t)y + (uint32_t)L * (uint32_t)z1;
+      load_rows<D>(static_cast<const uint8_t*>(lat.spins), L, tc.x0, row, row_y, row_z, rb);
+      const uint32_t e0 = eq_bits(rb.a, rb.ax) & vmask;
+      const uint32_t e1 = eq_bits(rb.a, rb.ay) & vmask;
+      A0 = e0 ? (e0 & bernoulli_word(g, sweep, 0, lat.t_bond, lat.key0, lat.key1)) : 0u;
+      A1 = e1 ? (e1 & bernoulli_word(g, sweep, 1, lat.t_bond, lat.key0, lat.key1)) : 0u;
+      lat.planes[g] = A0;
+      lat.planes[plane + g] = A1;
+      if (D == 3) {
+        const uint32_t e2 = eq_bits(rb.a, rb.az) & vmask;
+        A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, lat.key0, lat.key1)) : 0u;
+        lat.planes[2 * plane + g] = A2;
+      }
+    }
+    X = A0 & (vmask >> 1);          // x-bonds whose +x site is in the same word
+    S = ~(X << 1) & vmask;          // x-run starts
+    XW = (tc.x0 == 0 && L <= 32) ? ((A0 >> (L - 1)) & 1u) : 0u;  // wrap inside the word
+    Y = (y1 - tc.y0 >= 0 && y1 - tc.y0 < TY) ? A1 : 0u;
+    Z = (D == 3 && z1 - tc.z0 >= 0 && z1 - tc.z0 < TZ) ? A2 : 0u;
+    if (draws) {
+      // cluster draw of every site: word (i & 3) of Philox(i >> 2, sweep, DRAW, 0)
+      const uint32_t i0 = row * (uint32_t)L + (uint32_t)tc.x0;
+      uint32_t cached = 0xffffffffu;
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 4
+      for (int b = 0; b < nvalid; ++b) {
+        const uint32_t i = i0 + (uint32_t)b;
+        if ((i >> 2) != cached) {
+          cached = i >> 2;
+          w = philox(cached, sweep, kDraw, 0u, lat.key0, lat.key1);
+        }
+        sdraw[32 * r + b] = (uint8_t)draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.q);
+      }
+    }
+  }
+  sX[r] = X;
+  sS[r] = S;
+  __syncthreads();
+
+  // ---- phase 2: parent of every site = start of its x-run
+#pragma unroll 4
+  for (int k = 0; k < RPW; ++k) {
+    const int rr = warp + NW * k;
+    const uint32_t st = sS[rr];
+    const uint32_t t = (uint32_t)(32 * rr + lane);
+    par[t] = (st != 0u && lane < nvalid) ? (uint32_t)(32 * rr) + run_start(st, lane) : t;
+  }
+  __syncthreads();
+
+  // ---- phase 3: unions of runs joined by in-tile +y / +z bonds
+  if (rowv) {
+    if (Y) {
+      const int rn = r + (y1 - y);
+      const uint32_t Xn = sX[rn], Sn = sS[rn];
+      uint32_t U = Y & ~((Y & X & Xn) << 1);
+      while (U) {
+        const int b = __ffs(U) - 1;
+        U &= U - 1u;
+        sunion(par, (uint32_t)(32 * r) + run_start(S, b), (uint32_t)(32 * rn) + run_start(Sn, b), lat.err);
+      }
+    }
+    if (D == 3 && Z) {
+      const int rn = r + TY * (z1 - z);
+      const uint32_t Xn = sX[rn], Sn = sS[rn];
+      uint32_t U = Z & ~((Z & X & Xn) << 1);
+      while (U) {
+        const int b = __ffs(U) - 1;
+        U &= U - 1u;
+        sunion(par, (uint32_t)(32 * r) + run_start(S, b), (uint32_t)(32 * rn) + run_start(Sn, b), lat.err);
+      }
+    }
+    if (XW) sunion(par, (uint32_t)(32 * r) + run_start(S, L - 1), (uint32_t)(32 * r), lat.err);
+  }
+  __syncthreads();
+
+  // ---- phase 4: forest word of every site
+  const uint32_t lr_bit = 1u << lat.sbits;
+  const int shift = lat.sbits + 1;
+#pragma unroll 2
+  for (int k = 0; k < RPW; ++k) {
+    const int rr = warp + NW * k;
+    const int yy = tc.y0 + rr % TY, zz = tc.z0 + rr / TY;
+    if (sS[rr] == 0u || lane >= nvalid) continue;
+    const uint32_t t = (uint32_t)(32 * rr + lane);
+    const uint32_t lr = sfind(par, t);
+    const uint32_t lrow = lr >> 5;
+    const uint32_t gx = (uint32_t)tc.x0 + (lr & 31u);
+    const uint32_t gy = (uint32_t)tc.y0 + lrow % TY;
+    const uint32_t gz = (uint32_t)tc.z0 + lrow / TY;
+    const uint32_t gidx = gx + (uint32_t)L * (gy + (uint32_t)L * gz);
+    const uint32_t i = (uint32_t)(tc.x0 + lane) + (uint32_t)L * ((uint32_t)yy + (uint32_t)L * (uint32_t)zz);
+    const uint32_t draw = draws ? (uint32_t)sdraw[t] : 0u;
+    lat.forest[i] = (gidx << shift) | (lr == t ? lr_bit : 0u) | draw;
+  }
+}
+
+// ---------------------------------------------------------------- XY bonds
+template <int D>
+__global__ void __launch_bounds__(256) k_bonds_xy(Lattice lat, uint32_t sweep) {
+  __shared__ float s_phi;
+  if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
+  __syncthreads();
+  const float phi = s_phi;
+  const int L = lat.L, lane = threadIdx.x & 31;
+  const uint32_t nwords = lat.R * (uint32_t)lat.W;
+  const uint32_t plane = nwords;
+  const float* th = static_cast<const float*>(lat.spins);
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t g = gw; g < nwords; g += nw) {
+    const uint32_t row = g / (uint32_t)lat.W, xw = g % (uint32_t)lat.W;
+    const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
+    const int x = (int)(32 * xw) + lane;
+    uint32_t a = 0u;
+    if (x < L) {
+      const uint32_t i = (uint32_t)x + (uint32_t)L * row;
+      const uint4 w = philox(i, sweep, kBond, 0u, lat.key0, lat.key1);
+      uint32_t jn[3];
+      jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
+      jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
+      jn[2] = (D == 3) ? ((z + 1 == (uint32_t)L) ? i - z * L * L : i + (uint32_t)L * L) : 0u;
+      const float xi = cosf(__fsub_rn(th[i], phi));
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float xj = cosf(__fsub_rn(th[jn[d]], phi));
+        const float prod = __fmul_rn(xi, xj);
+        bool act = false;
+        if (prod > 0.0f) {
+          const float p = -expm1f(-__fmul_rn(lat.twoK, prod));
+          const float u = __fmul_rn((float)(word_of(w, d) >> 8), 0x1p-24f);
+          act = u < p;
+        }
+        a |= (uint32_t)act << d;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const uint32_t bal = __ballot_sync(kFull, (a >> d) & 1u);
+      if (lane == d) lat.planes[d * plane + g] = bal;
+    }
+  }
+}
+
+}  // namespace
+
+void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz) {
+  *ntx = (L + 31) / 32;
+  if (dim == 2) {
+    *nty = (L + kTile2Y - 1) / kTile2Y;
+    *ntz = 1;
+  } else {
+    *nty = (L + kTile3Y - 1) / kTile3Y;
+    *ntz = (L + kTile3Z - 1) / kTile3Z;
+  }
+}
+
+cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st) {
+  const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
+  if (lat.dim == 2) {
+    if (from_mask) k_label<2, true><<<g, kTileThreads, 0, st>>>(lat, sweep);
+    else k_label<2, false><<<g, kTileThreads, 0, st>>>(lat, sweep);
+  } else {
+    if (from_mask) k_label<3, true><<<g, kTileThreads, 0, st>>>(lat, sweep);
+    else k_label<3, false><<<g, kTileThreads, 0, st>>>(lat, sweep);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, cudaStream_t st) {
+  const uint32_t words = lat.R * (uint32_t)lat.W;
+  unsigned g = (words + 7u) / 8u;
+  if (g > 4096u) g = 4096u;
+  if (lat.dim == 2) k_bonds_xy<2><<<g, 256, 0, st>>>(lat, sweep);
+  else k_bonds_xy<3><<<g, 256, 0, st>>>(lat, sweep);
+  return cudaGetLastError();
+}
+
+}  // namespace swgb

@@ -87,7 +87,7 @@ int sw_label_from_bonds_noalloc(int dim, int L, const uint32_t* dev_mask, int32_
 
   int flag = 0;
   cudaError_t e = cudaMemsetAsync(lat.err, 0, sizeof(int), st);  // the flag must start at zero
-  if (e == cudaSuccess) e = swgb::launch_bond_label(lat, swgb::kIsing, 0u, true, st);
+  if (e == cudaSuccess) e = swgb::launch_label(lat, 0u, true, st);
   if (e == cudaSuccess) e = swgb::launch_merge(lat, st);
   if (e == cudaSuccess) e = swgb::launch_labels_out(lat, dev_labels, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, lat.err, sizeof(int), cudaMemcpyDeviceToHost, st);
