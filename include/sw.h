@@ -180,8 +180,10 @@ int sw_label_from_bonds(sw_handle* h, const uint32_t* host_mask, int32_t* host_l
 /* One measured sweep, like sw_sweep(h, 1), with CUDA events recorded on
  * the handle's stream between its kernels.  Synchronises, then writes the
  * device time of each phase in milliseconds to phase_ms[0..3]:
- * [0] bonds + tile labels, [1] tile-boundary merge, [2] flip, [3]
- * measurement.  nphase must be >= 4.  For profiling. */
+ * [0] bonds + tile labels (Ising/Potts: including the measurement of the
+ * incoming state, the previous sweep's record), [1] tile-boundary merge,
+ * [2] flip, [3] stand-alone measurement (XY only; 0 otherwise).  nphase must
+ * be >= 4.  For profiling. */
 int sw_sweep_timed(sw_handle* h, float* phase_ms, int nphase);
 
 /* Records of measured sweeps first .. first+count-1 into a host array.  The

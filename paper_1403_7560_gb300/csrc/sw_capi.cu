@@ -46,6 +46,7 @@ struct sw_handle {
   bool own_stream = false;
   Lattice lat{};
   Measure meas{};
+  uint64_t pending = 0;         // measured sweep whose record is not yet written
   int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
   void* d_block = nullptr;      // one allocation holding every small buffer
 };
@@ -94,14 +95,51 @@ int check_device_error(sw_handle* h) {
 }
 
 // Step (1) and the tile half of step (2): Ising/Potts bonds are drawn inside
-// the labeling kernel; XY bonds come from their own kernel first.
-cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k) {
+// the labeling kernel, which also measures the incoming state when the
+// previous sweep's record is pending; XY bonds come from their own kernel.
+// Sets *finalize to the pending sweep whose record the flip kernel of this
+// sweep must write (0 if none).
+cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k, uint32_t* finalize) {
+  *finalize = 0u;
   if (h->model == SW_XY) {
     cudaError_t e = swgb::launch_bonds_xy(h->lat, k, h->stream);
     if (e != cudaSuccess) return e;
     return swgb::launch_label(h->lat, k, true, h->stream);
   }
+  if (h->pending) {
+    *finalize = (uint32_t)h->pending;
+    h->pending = 0;
+    return swgb::launch_label_measured(h->lat, k, h->meas, h->stream);
+  }
   return swgb::launch_label(h->lat, k, false, h->stream);
+}
+
+// Write the record of a pending measured sweep with the stand-alone kernel.
+cudaError_t flush_pending(sw_handle* h) {
+  if (!h->pending) return cudaSuccess;
+  const uint32_t k = (uint32_t)h->pending;
+  h->pending = 0;
+  return swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+}
+
+// One sweep; Ising/Potts leave their measurement pending (it is taken from
+// the next sweep's labeling kernel or by flush_pending), XY measures at once.
+cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
+  cudaError_t e = cudaSuccess;
+  uint32_t finalize = 0u;
+  if (ev) e = cudaEventRecord(ev[0], h->stream);
+  if (e == cudaSuccess) e = launch_bonds_labels(h, k, &finalize);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], h->stream);
+  if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], h->stream);
+  if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas, measure, finalize, h->stream);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->stream);
+  if (e == cudaSuccess && measure) {
+    if (h->model == SW_XY) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+    else h->pending = k;
+  }
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], h->stream);
+  return e;
 }
 
 int run_sweeps(sw_handle* h, int n, bool measure) {
@@ -110,11 +148,7 @@ int run_sweeps(sw_handle* h, int n, bool measure) {
   for (int s = 0; s < n; ++s) {
     if (h->sweep >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
     const uint32_t k = (uint32_t)(++h->sweep);
-    cudaError_t e = launch_bonds_labels(h, k);
-    if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
-    if (e == cudaSuccess)
-      e = swgb::launch_flip(h->lat, h->model, k, measure ? h->meas.nclusters : nullptr, h->stream);
-    if (e == cudaSuccess && measure) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+    const cudaError_t e = one_sweep(h, k, measure, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   }
   return SW_OK;
@@ -158,18 +192,19 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   lat.twoK = (float)(2.0 / T);
   lat.key0 = (uint32_t)(seed & 0xffffffffu);
   lat.key1 = (uint32_t)(seed >> 32);
+  lat.model = model;
   h->bond_words = (size_t)dim * lat.R * (size_t)lat.W;
 
   cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { cuda_fail(e, "stream"); release(h); return nullptr; }
   h->own_stream = true;
 
-  // small buffers, carved from one block: err, ticket, nclusters, acc,
-  // hist, partials, series ring
-  const size_t off_err = 0, off_ticket = 16, off_ncl = 32, off_acc = 64;
-  const size_t off_hist = off_acc + 64;
-  const size_t off_pi = off_hist + 256 * 8;
-  const size_t off_pd = off_pi + 2 * 8 * (size_t)swgb::kMeasureBlocks;
+  // small buffers, carved from one block: err, cluster counts, slot sums,
+  // slot histograms, XY partials, accumulators, series ring
+  const size_t off_err = 0, off_ncl = 64, off_acc = 128;
+  const size_t off_sums = 256;
+  const size_t off_hist = off_sums + 16 * (size_t)swgb::kSlots;
+  const size_t off_pd = off_hist + 8 * 256 * (size_t)swgb::kSlots;
   const size_t off_series = off_pd + 3 * 8 * (size_t)swgb::kMeasureBlocks;
   const size_t block_bytes = off_series + sizeof(swgb::Record) * (size_t)kSeriesCap;
 
@@ -185,12 +220,12 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   }
   char* blk = static_cast<char*>(h->d_block);
   lat.err = reinterpret_cast<int*>(blk + off_err);
-  h->meas.ticket = reinterpret_cast<unsigned int*>(blk + off_ticket);
   h->meas.nclusters = reinterpret_cast<unsigned long long*>(blk + off_ncl);
-  h->meas.acc = reinterpret_cast<double*>(blk + off_acc);
+  h->meas.sums = reinterpret_cast<unsigned long long*>(blk + off_sums);
   h->meas.hist = reinterpret_cast<unsigned long long*>(blk + off_hist);
-  h->meas.part_i = reinterpret_cast<long long*>(blk + off_pi);
+  h->meas.acc = reinterpret_cast<double*>(blk + off_acc);
   h->meas.part_d = reinterpret_cast<double*>(blk + off_pd);
+  h->meas.xy_blocks = 0;
   h->meas.series = blk + off_series;
   h->meas.series_cap = kSeriesCap;
 
@@ -228,15 +263,7 @@ int sw_sweep_timed(sw_handle* h, float* phase_ms, int nphase) {
     return cuda_fail(e, "event");
   }
   const uint32_t k = (uint32_t)(++h->sweep);
-  e = cudaEventRecord(ev[0], h->stream);
-  if (e == cudaSuccess) e = launch_bonds_labels(h, k);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-  if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
-  if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas.nclusters, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
-  if (e == cudaSuccess) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
+  e = one_sweep(h, k, true, ev);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
   for (int p = 0; p < 4 && e == cudaSuccess; ++p) e = cudaEventElapsedTime(&phase_ms[p], ev[p], ev[p + 1]);
   for (int p = 0; p < 5; ++p) cudaEventDestroy(ev[p]);
@@ -254,7 +281,8 @@ int sw_sync(sw_handle* h) {
 int sw_measure(sw_handle* h, sw_moments* out) {
   if (!h || !out) return fail(SW_ERR_BAD_ARG, "NULL argument");
   double acc[6];
-  cudaError_t e = cudaMemcpyAsync(acc, h->meas.acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = flush_pending(h);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, h->meas.acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->meas.acc, 0, sizeof(acc), h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "measure copy");
   const int rc = check_device_error(h);
@@ -292,6 +320,8 @@ uint64_t sw_sweep_counter(sw_handle* h) { return h ? h->sweep : 0; }
 int sw_set_sweep_counter(sw_handle* h, uint64_t k) {
   if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
   if (k >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter must be < 2^32 - 1");
+  const cudaError_t e = flush_pending(h);
+  if (e != cudaSuccess) return cuda_fail(e, "pending measurement");
   h->sweep = k;
   return SW_OK;
 }
@@ -311,7 +341,8 @@ int sw_get_spins(sw_handle* h, void* host, size_t bytes) {
 int sw_set_spins(sw_handle* h, const void* host, size_t bytes) {
   if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
   if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
-  cudaError_t e = cudaMemcpyAsync(h->lat.spins, host, bytes, cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = flush_pending(h);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->lat.spins, host, bytes, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_spins");
   return check_device_error(h);
 }
@@ -326,7 +357,8 @@ int sw_get_spins_device(sw_handle* h, void* dev, size_t bytes) {
 int sw_set_spins_device(sw_handle* h, const void* dev, size_t bytes) {
   if (!h || !dev) return fail(SW_ERR_BAD_ARG, "NULL argument");
   if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
-  cudaError_t e = cudaMemcpyAsync(h->lat.spins, dev, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaError_t e = flush_pending(h);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->lat.spins, dev, bytes, cudaMemcpyDeviceToDevice, h->stream);
   return e == cudaSuccess ? SW_OK : cuda_fail(e, "set_spins_device");
 }
 
@@ -362,6 +394,8 @@ int sw_label_from_bonds(sw_handle* h, const uint32_t* host_mask, int32_t* host_l
 int sw_get_series(sw_handle* h, uint64_t first, size_t count, sw_record* host) {
   if (!h || (!host && count)) return fail(SW_ERR_BAD_ARG, "NULL argument");
   if (count > (size_t)kSeriesCap) return fail(SW_ERR_RANGE, "count exceeds the retained series");
+  const cudaError_t fe = flush_pending(h);
+  if (fe != cudaSuccess) return cuda_fail(fe, "pending measurement");
   const int rc = check_device_error(h);
   if (rc != SW_OK) return rc;
   static_assert(sizeof(swgb::Record) == sizeof(sw_record), "record layout");

@@ -231,5 +231,112 @@ __device__ __forceinline__ T block_combine(T warp_total, T* scratch) {
   return r;
 }
 
+// ---------------------------------------------------------------- records
+// Add a block's integer M, E (any thread's share) into its slot; called by
+// all threads of the block.
+template <int NW>
+__device__ __forceinline__ void add_integer_sums(const Measure& mb, long long m, long long e,
+                                                 long long* s_red) {
+  const long long M = block_combine<NW>(warp_sum(m), s_red);
+  const long long E = block_combine<NW>(warp_sum(e), s_red);
+  if (threadIdx.x == 0) {
+    unsigned long long* slot = mb.sums + 2 * (blockIdx.x % kSlots);
+    if (M) atomicAdd(&slot[0], (unsigned long long)M);
+    if (E) atomicAdd(&slot[1], (unsigned long long)E);
+  }
+}
+
+// Add a block's Potts histogram (shared bins) into its slot.
+__device__ __forceinline__ void add_histogram(const Lattice& lat, const Measure& mb,
+                                              const unsigned int* s_hist) {
+  unsigned long long* slot = mb.hist + 256 * (blockIdx.x % kSlots);
+  for (int k = threadIdx.x; k < lat.q; k += blockDim.x)
+    if (s_hist[k]) atomicAdd(&slot[k], (unsigned long long)s_hist[k]);
+}
+
+// Record of `sweep` and the FP64 accumulators, from the slot sums (Ising /
+// Potts) or the XY per-block partials, summed in a fixed order; the slots
+// and the sweep's cluster count are reset.  Called by all threads of ONE
+// block of a kernel that runs after every kernel that added to the sums.
+// Every double operation rounds to nearest, no contraction.
+template <int NW>
+__device__ __forceinline__ void finalize_record(const Lattice& lat, const Measure& mb, uint32_t sweep,
+                                                long long* s_ri, double* s_rd) {
+  long long M = 0, E = 0, S2 = 0;
+  double mx = 0.0, my = 0.0, exy = 0.0;
+  if (lat.model == kXY) {
+    double a = 0.0, c = 0.0, g = 0.0;
+    for (int k = threadIdx.x; k < mb.xy_blocks; k += blockDim.x) {
+      a = __dadd_rn(a, __ldcg(&mb.part_d[3 * k + 0]));
+      c = __dadd_rn(c, __ldcg(&mb.part_d[3 * k + 1]));
+      g = __dadd_rn(g, __ldcg(&mb.part_d[3 * k + 2]));
+    }
+    mx = block_combine<NW>(warp_sum(a), s_rd);
+    my = block_combine<NW>(warp_sum(c), s_rd);
+    exy = block_combine<NW>(warp_sum(g), s_rd);
+  } else {
+    long long a = 0, c = 0, g = 0;
+    for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {
+      a += (long long)__ldcg(&mb.sums[2 * k + 0]);
+      c += (long long)__ldcg(&mb.sums[2 * k + 1]);
+      mb.sums[2 * k + 0] = 0ull;
+      mb.sums[2 * k + 1] = 0ull;
+    }
+    if (lat.model == kPotts) {
+      // n[k] = sum over slots, all (slot, k) pairs spread over the block
+      __shared__ unsigned long long s_n[256];
+      for (int k = threadIdx.x; k < 256; k += blockDim.x) s_n[k] = 0ull;
+      __syncthreads();
+      for (int t = threadIdx.x; t < kSlots * lat.q; t += blockDim.x) {
+        const int sl = t / lat.q, k = t % lat.q;
+        const unsigned long long v = __ldcg(&mb.hist[256 * sl + k]);
+        if (v) {
+          atomicAdd(&s_n[k], v);
+          mb.hist[256 * sl + k] = 0ull;
+        }
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < lat.q; k += blockDim.x) g += (long long)(s_n[k] * s_n[k]);
+    }
+    M = block_combine<NW>(warp_sum(a), s_ri);
+    E = block_combine<NW>(warp_sum(c), s_ri);
+    S2 = block_combine<NW>(warp_sum(g), s_ri);
+  }
+  if (threadIdx.x != 0) return;
+  unsigned long long* ncl_slot = mb.nclusters + (sweep & 1u);
+  const long long ncl = (long long)__ldcg(ncl_slot);
+  *ncl_slot = 0ull;
+  double M2, Ed;
+  if (lat.model == kIsing) {
+    M2 = __dmul_rn((double)M, (double)M);
+    Ed = (double)E;
+  } else if (lat.model == kPotts) {
+    const long long N = (long long)lat.N;
+    M2 = __ddiv_rn((double)((long long)lat.q * S2 - N * N), (double)(lat.q - 1));
+    Ed = (double)E;
+  } else {
+    M2 = __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my));
+    Ed = exy;
+  }
+  Record* rec = static_cast<Record*>(mb.series) + (sweep % (uint32_t)mb.series_cap);
+  rec->sweep = sweep;
+  rec->M = M;
+  rec->E = E;
+  rec->nclusters = ncl;
+  rec->S2 = S2;
+  rec->mx = mx;
+  rec->my = my;
+  rec->e_xy = exy;
+  rec->M2 = M2;
+  rec->Ed = Ed;
+  double* acc = mb.acc;
+  acc[0] = __dadd_rn(acc[0], 1.0);
+  acc[1] = __dadd_rn(acc[1], M2);
+  acc[2] = __dadd_rn(acc[2], __dmul_rn(M2, M2));
+  acc[3] = __dadd_rn(acc[3], Ed);
+  acc[4] = __dadd_rn(acc[4], __dmul_rn(Ed, Ed));
+  acc[5] = __dadd_rn(acc[5], (double)ncl);
+}
+
 }  // namespace dev
 }  // namespace swgb

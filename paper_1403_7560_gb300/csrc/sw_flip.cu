@@ -24,8 +24,18 @@ namespace {
 using namespace dev;
 
 template <int D>
+struct MergeShape {
+  // face bonds a tile owns: +x face, +y face (and +z face)
+  static constexpr int kMax = Tile<D>::ROWS + 32 * Tile<D>::TZ + (D == 3 ? 32 * Tile<D>::TY : 0);
+  static constexpr int kPerThread = (kMax + kTileThreads - 1) / kTileThreads;
+};
+
+template <int D>
 __global__ void __launch_bounds__(kTileThreads) k_merge(Lattice lat) {
   constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  constexpr int NC = MergeShape<D>::kPerThread;
+  __shared__ uint2 s_list[MergeShape<D>::kMax];
+  __shared__ int s_n;
   const TileCoord tc = tile_coord<D>(lat);
   const int L = lat.L;
   const int shift = lat.sbits + 1;
@@ -33,9 +43,20 @@ __global__ void __launch_bounds__(kTileThreads) k_merge(Lattice lat) {
   const int cx = (lat.ntx > 1) ? ny * nz : 0;
   const int cy = (lat.nty > 1) ? nx * nz : 0;
   const int cz = (D == 3 && lat.ntz > 1) ? nx * ny : 0;
+  const int total = cx + cy + cz;
   const uint32_t plane = lat.R * (uint32_t)lat.W;
   const int lane = threadIdx.x & 31;
-  for (int c = threadIdx.x; c < cx + cy + cz; c += blockDim.x) {
+  if (threadIdx.x == 0) s_n = 0;
+
+  // this thread's face bonds: bond bits first, then both forest words
+  uint32_t ii[NC], jj[NC], a[NC], b[NC];
+  bool on[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int c = threadIdx.x + k * kTileThreads;
+    on[k] = false;
+    ii[k] = jj[k] = 0u;
+    if (c >= total) continue;
     int x, y, z, d;
     if (c < cx) {
       d = 0; x = tc.x0 + nx - 1; y = tc.y0 + c % ny; z = tc.z0 + c / ny;
@@ -49,27 +70,47 @@ __global__ void __launch_bounds__(kTileThreads) k_merge(Lattice lat) {
     if (D == 2) z = 0;
     const uint32_t row = (uint32_t)y + (uint32_t)L * (uint32_t)z;
     const uint32_t bits = __ldg(&lat.planes[d * plane + row * lat.W + (x >> 5)]);
-    if (!((bits >> (x & 31)) & 1u)) continue;
+    on[k] = (bits >> (x & 31)) & 1u;
     const uint32_t i = (uint32_t)x + (uint32_t)L * row;
-    uint32_t j;
-    if (d == 0) j = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
-    else if (d == 1) j = (y + 1 == L) ? i - (uint32_t)y * L : i + (uint32_t)L;
-    else j = (z + 1 == L) ? i - (uint32_t)z * L * L : i + (uint32_t)L * L;
-    const uint32_t a = __ldcg(&lat.forest[i]) >> shift;
-    const uint32_t b = __ldcg(&lat.forest[j]) >> shift;
-    if (a == b) continue;
-    const unsigned long long key = ((unsigned long long)a << 32) | b;
-    const unsigned grp = __match_any_sync(__activemask(), key);
-    if (lane == __ffs(grp) - 1) gunion(lat.forest, a, b, lat.sbits, lat.err);
+    ii[k] = i;
+    if (d == 0) jj[k] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
+    else if (d == 1) jj[k] = (y + 1 == L) ? i - (uint32_t)y * L : i + (uint32_t)L;
+    else jj[k] = (z + 1 == L) ? i - (uint32_t)z * L * L : i + (uint32_t)L * L;
   }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    a[k] = on[k] ? __ldcg(&lat.forest[ii[k]]) >> shift : 0u;
+    b[k] = on[k] ? __ldcg(&lat.forest[jj[k]]) >> shift : 0u;
+  }
+  __syncthreads();
+  // distinct (root, root) pairs of each warp go to the tile's work list
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const bool want = on[k] && a[k] != b[k];
+    const unsigned long long key = ((unsigned long long)a[k] << 32) | b[k];
+    const unsigned grp = __match_any_sync(kFull, want ? key : ~0ull);
+    if (want && lane == __ffs(grp) - 1) s_list[atomicAdd(&s_n, 1)] = make_uint2(a[k], b[k]);
+  }
+  __syncthreads();
+  const int n = s_n;
+  for (int e = threadIdx.x; e < n; e += kTileThreads) gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err);
 }
 
+constexpr int kFlipThreads = 256;
+constexpr int kFlipBatch = 8;  // rows whose loads and root walks advance together
+
 template <int MODEL, int D>
-__global__ void __launch_bounds__(kTileThreads) k_flip(Lattice lat, uint32_t sweep,
-                                                        unsigned long long* nclusters) {
-  constexpr int TY = Tile<D>::TY, ROWS = Tile<D>::ROWS, NW = kTileThreads / 32, RPW = ROWS / NW;
+__global__ void __launch_bounds__(kFlipThreads) k_flip(Lattice lat, uint32_t sweep, Measure mb,
+                                                        bool count, uint32_t finalize) {
+  constexpr int TY = Tile<D>::TY, ROWS = Tile<D>::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
+  constexpr int B = kFlipBatch;
+  static_assert(RPW % B == 0, "rows per warp must be a multiple of the batch");
   __shared__ float s_phi;
   __shared__ long long s_red[NW];
+  __shared__ double s_rd[NW];
+  // the record of the previous measured sweep, from the sums its successor's
+  // labeling kernel left behind
+  if (finalize != 0u && blockIdx.x == 0) finalize_record<NW>(lat, mb, finalize, s_red, s_rd);
   if (MODEL == kXY) {
     if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
     __syncthreads();
@@ -82,57 +123,87 @@ __global__ void __launch_bounds__(kTileThreads) k_flip(Lattice lat, uint32_t swe
   const int x = tc.x0 + lane;
   long long roots = 0;
 
-  // local roots: walk to the global root, store (root, marker, root draw)
+  // local roots walk to their global root and store (root, marker, draw);
+  // the loads and walks of B rows advance together
 #pragma unroll 1
-  for (int k = 0; k < RPW; ++k) {
-    const int rr = warp + NW * k;
-    const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
-    if (x >= L || y >= L || (D == 3 && z >= L)) continue;
-    const uint32_t i = (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
-    const uint32_t f = __ldcg(&lat.forest[i]);
-    if (!(f & lr_bit)) continue;
-    uint32_t cur = i, v = f;
-    int it = 0;
-    for (; it < (1 << 22); ++it) {
-      const uint32_t p = v >> shift;
-      if (p == cur) break;
-      cur = p;
-      v = __ldcg(&lat.forest[cur]);
+  for (int k0 = 0; k0 < RPW; k0 += B) {
+    uint32_t idx[B], cur[B], v[B];
+    bool pend[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int rr = warp + NW * (k0 + k);
+      const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
+      const bool ok = x < L && y < L && (D == 2 || z < L);
+      idx[k] = ok ? (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z) : 0u;
+      v[k] = ok ? __ldcg(&lat.forest[idx[k]]) : 0u;
+      const bool lr = ok && (v[k] & lr_bit);
+      pend[k] = lr && (v[k] >> shift) != idx[k];
+      if (lr && !pend[k]) ++roots;
+      cur[k] = v[k] >> shift;
     }
-    if (it == (1 << 22)) atomicExch(lat.err, kErrTimeout);
-    if (cur == i) ++roots;
-    else __stcg(&lat.forest[i], (cur << shift) | lr_bit | (v & dmask));
+    for (int it = 0; it < (1 << 22); ++it) {
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < B; ++k)
+        if (pend[k]) v[k] = __ldcg(&lat.forest[cur[k]]);
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        if (!pend[k]) continue;
+        const uint32_t p = v[k] >> shift;
+        if (p == cur[k]) {
+          pend[k] = false;
+          __stcg(&lat.forest[idx[k]], (cur[k] << shift) | lr_bit | (v[k] & dmask));
+        } else {
+          cur[k] = p;
+          any = true;
+        }
+      }
+      if (!any) break;
+      if (it == (1 << 22) - 1) atomicExch(lat.err, kErrTimeout);
+    }
   }
   __syncthreads();
 
-  // every site: the draw of its cluster from its local root's word
+  // every site: its cluster's draw from its local root's word
 #pragma unroll 1
-  for (int k = 0; k < RPW; ++k) {
-    const int rr = warp + NW * k;
-    const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
-    if (x >= L || y >= L || (D == 3 && z >= L)) continue;
-    const uint32_t i = (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
-    uint32_t v = __ldcg(&lat.forest[i]);
-    if (!(v & lr_bit)) v = __ldcg(&lat.forest[v >> shift]);
-    const uint32_t draw = v & dmask;
-    if (MODEL == kIsing) {
-      static_cast<int8_t*>(lat.spins)[i] = draw ? (int8_t)-1 : (int8_t)1;
-    } else if (MODEL == kPotts) {
-      static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)draw;
-    } else if (draw) {
-      float* th = static_cast<float*>(lat.spins);
-      const float phi = s_phi;
-      const float two_pi = 0x1.921fb6p+2f, pi = 0x1.921fb6p+1f;
-      float t = __fsub_rn(__fadd_rn(__fmul_rn(2.0f, phi), pi), th[i]);
-      if (t >= two_pi) t = __fsub_rn(t, two_pi);
-      if (t >= two_pi) t = __fsub_rn(t, two_pi);
-      if (t < 0.0f) t = __fadd_rn(t, two_pi);
-      th[i] = t;
+  for (int k0 = 0; k0 < RPW; k0 += B) {
+    uint32_t idx[B], v[B];
+    bool ok[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int rr = warp + NW * (k0 + k);
+      const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
+      ok[k] = x < L && y < L && (D == 2 || z < L);
+      idx[k] = ok[k] ? (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z) : 0u;
+      v[k] = ok[k] ? __ldcg(&lat.forest[idx[k]]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (ok[k] && !(v[k] & lr_bit)) v[k] = __ldcg(&lat.forest[v[k] >> shift]);
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (!ok[k]) continue;
+      const uint32_t draw = v[k] & dmask;
+      const uint32_t i = idx[k];
+      if (MODEL == kIsing) {
+        static_cast<int8_t*>(lat.spins)[i] = draw ? (int8_t)-1 : (int8_t)1;
+      } else if (MODEL == kPotts) {
+        static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)draw;
+      } else if (draw) {
+        float* th = static_cast<float*>(lat.spins);
+        const float phi = s_phi;
+        const float two_pi = 0x1.921fb6p+2f, pi = 0x1.921fb6p+1f;
+        float t = __fsub_rn(__fadd_rn(__fmul_rn(2.0f, phi), pi), th[i]);
+        if (t >= two_pi) t = __fsub_rn(t, two_pi);
+        if (t >= two_pi) t = __fsub_rn(t, two_pi);
+        if (t < 0.0f) t = __fadd_rn(t, two_pi);
+        th[i] = t;
+      }
     }
   }
-  if (nclusters) {
+  if (count) {
     const long long tot = block_combine<NW>(warp_sum(roots), s_red);
-    if (threadIdx.x == 0 && tot) atomicAdd(nclusters, (unsigned long long)tot);
+    if (threadIdx.x == 0 && tot) atomicAdd(mb.nclusters + (sweep & 1u), (unsigned long long)tot);
   }
 }
 
@@ -160,17 +231,17 @@ cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep,
-                        unsigned long long* nclusters, cudaStream_t st) {
+cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
+                        uint32_t finalize, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
   if (lat.dim == 2) {
-    if (model == kIsing) k_flip<kIsing, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, nclusters);
-    else if (model == kPotts) k_flip<kPotts, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, nclusters);
-    else k_flip<kXY, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, nclusters);
+    if (model == kIsing) k_flip<kIsing, 2><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
+    else if (model == kPotts) k_flip<kPotts, 2><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
+    else k_flip<kXY, 2><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
   } else {
-    if (model == kIsing) k_flip<kIsing, 3><<<g, kTileThreads, 0, st>>>(lat, sweep, nclusters);
-    else if (model == kPotts) k_flip<kPotts, 3><<<g, kTileThreads, 0, st>>>(lat, sweep, nclusters);
-    else k_flip<kXY, 3><<<g, kTileThreads, 0, st>>>(lat, sweep, nclusters);
+    if (model == kIsing) k_flip<kIsing, 3><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
+    else if (model == kPotts) k_flip<kPotts, 3><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
+    else k_flip<kXY, 3><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
   }
   return cudaGetLastError();
 }

@@ -26,15 +26,20 @@ struct Lattice {
   uint32_t t_bond;      // Ising/Potts: bond active iff draw < t_bond
   float twoK;           // XY: 2/T as float
   uint32_t key0, key1;  // Philox key = seed
+  int model;            // Model
 };
 
 // Buffers of the moment reduction (the per-sweep record and accumulators).
+// Integer sums are spread over kSlots slots (by block index) so that no
+// single word takes an atomic from every block; the record is finalised by
+// one block of a later kernel in the same stream.
+constexpr int kSlots = 64;
 struct Measure {
-  unsigned long long* nclusters;  // roots counted by the flip kernel
-  unsigned long long* hist;       // Potts histogram [q]
-  long long* part_i;              // per-block integer partials [2 * nblk]
-  double* part_d;                 // per-block float partials [3 * nblk]
-  unsigned int* ticket;           // blocks finished (last-block pattern)
+  unsigned long long* nclusters;  // roots counted by the flip kernel, [2] by sweep parity
+  unsigned long long* sums;       // [kSlots][2]: integer M, E (two's complement)
+  unsigned long long* hist;       // [kSlots][256]: Potts histogram
+  double* part_d;                 // XY per-block partials [3 * kMeasureBlocks]
+  int xy_blocks;                  // blocks that wrote part_d
   double* acc;                    // n, sum M2, M4, E, E2, nclusters
   void* series;                   // sw_record ring
   int series_cap;
@@ -67,9 +72,18 @@ cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, cudaStream_t st)
 // Tile labels (+ Ising/Potts bonds when from_mask is false; cluster draws
 // when sweep != 0) into the forest.
 cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st);
+// Same for Ising/Potts, also measuring the incoming spins (the state after
+// sweep - 1) into the record of sweep - 1.
+cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Measure& m,
+                                  cudaStream_t st);
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st);
-cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep,
-                        unsigned long long* nclusters, cudaStream_t st);
+// Flip of `sweep`; counts roots into m.nclusters[sweep & 1] when `count`;
+// when finalize != 0 its first block first writes the record of sweep
+// `finalize` from the sums a previous kernel left in m.
+cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
+                        uint32_t finalize, cudaStream_t st);
+// Stand-alone measurement of the current spins as the record of `sweep`
+// (sums, then a one-block finalisation).
 cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const Measure& m,
                            cudaStream_t st);
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);

@@ -13,6 +13,8 @@
 //     the previous bit are skipped).
 //   phase 4 (lane per site): find the tile-local root and write the forest
 //     word (root as a global index, local-root marker, cluster draw).
+//   With MEASURE the row threads also measure the incoming spins (the state
+//   after the previous sweep) from the same bytes and equality masks.
 // k_bonds_xy: XY bonds (lane per site): project on the sweep's mirror axis
 //   and test the embedded-Ising probability; ballot into the bit-planes.
 #include "sw_device.cuh"
@@ -21,6 +23,8 @@ namespace swgb {
 namespace {
 
 using namespace dev;
+
+constexpr int kSmallQ = 16;  // Potts histograms up to this q are counted per thread
 
 // The 32 spin bytes of a row word and of its +x, +y, +z neighbour words.
 struct RowBytes {
@@ -72,14 +76,30 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
   }
 }
 
-template <int D, bool FROM_MASK>
-__global__ void __launch_bounds__(kTileThreads) k_label(Lattice lat, uint32_t sweep) {
+// MM (measurement mode) 1 = Ising, 2 = Potts: also measure the incoming
+// spins (the state after sweep - 1): M and E from the row words' equality
+// masks and the Potts histogram, added to the measurement slots (the flip
+// kernel of this sweep writes the record of sweep - 1).  MM = 0: none.
+template <int D, bool FROM_MASK, int MM>
+__global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t sweep, Measure mb) {
+  constexpr bool MEASURE = MM != 0;
   constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ, ROWS = Tile<D>::ROWS;
   constexpr int NW = kTileThreads / 32, RPW = ROWS / NW;
   static_assert(ROWS == kTileThreads, "one thread per row word");
+  static_assert(!(MEASURE && FROM_MASK), "measurement needs the spins");
   __shared__ uint32_t par[ROWS * 32];
   __shared__ uint8_t sdraw[ROWS * 32];
   __shared__ uint32_t sX[ROWS], sS[ROWS];
+  // Potts histogram: per-warp bins for q <= kSmallQ, shared bins above
+  __shared__ unsigned int s_hist[MM == 2 ? 256 : 1];
+  __shared__ unsigned int s_whist[MM == 2 ? NW * kSmallQ : 1];
+  __shared__ long long s_red[NW];
+  int m_acc = 0, e_acc = 0;
+  if (MM == 2) {
+    for (int k = threadIdx.x; k < 256; k += kTileThreads) s_hist[k] = 0u;
+    for (int k = threadIdx.x; k < NW * kSmallQ; k += kTileThreads) s_whist[k] = 0u;
+    __syncthreads();
+  }
 
   const TileCoord tc = tile_coord<D>(lat);
   const int L = lat.L;
@@ -110,17 +130,43 @@ __global__ void __launch_bounds__(kTileThreads) k_label(Lattice lat, uint32_t sw
       const uint32_t row_y = (uint32_t)y1 + (uint32_t)L * (uint32_t)z;
       const uint32_t row_z = (uint32_t)y + (uint32_t)L * (uint32_t)z1;
       load_rows<D>(static_cast<const uint8_t*>(lat.spins), L, tc.x0, row, row_y, row_z, rb);
+      // equality masks (and the measurement) first, so the row bytes are
+      // dead before the Bernoulli words are drawn
       const uint32_t e0 = eq_bits(rb.a, rb.ax) & vmask;
       const uint32_t e1 = eq_bits(rb.a, rb.ay) & vmask;
+      const uint32_t e2 = (D == 3) ? (eq_bits(rb.a, rb.az) & vmask) : 0u;
+      if (MM == 1) {
+        // M = #(+1) - #(-1);  E = -(#parallel - #antiparallel) over the +d bonds
+        uint32_t ones[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ones[k] = 0x01010101u;
+        const int par_bonds = __popc(e0) + __popc(e1) + (D == 3 ? __popc(e2) : 0);
+        m_acc += 2 * __popc(eq_bits(rb.a, ones) & vmask) - nvalid;
+        e_acc -= 2 * par_bonds - D * nvalid;
+      } else if (MM == 2) {
+        // E = number of unequal +d bonds; histogram n[k] of the states
+        const int par_bonds = __popc(e0) + __popc(e1) + (D == 3 ? __popc(e2) : 0);
+        e_acc += D * nvalid - par_bonds;
+        if (lat.q <= kSmallQ) {
+          for (int k = 0; k < lat.q; ++k) {
+            uint32_t kk[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) kk[j] = 0x01010101u * (uint32_t)k;
+            const unsigned c = (unsigned)__popc(eq_bits(rb.a, kk) & vmask);
+            if (c) atomicAdd(&s_whist[warp * kSmallQ + k], c);
+          }
+        } else {
+#pragma unroll
+          for (int b = 0; b < 32; ++b)
+            if (b < nvalid) atomicAdd(&s_hist[(rb.a[b >> 2] >> (8 * (b & 3))) & 0xffu], 1u);
+        }
+      }
       A0 = e0 ? (e0 & bernoulli_word(g, sweep, 0, lat.t_bond, lat.key0, lat.key1)) : 0u;
       A1 = e1 ? (e1 & bernoulli_word(g, sweep, 1, lat.t_bond, lat.key0, lat.key1)) : 0u;
+      if (D == 3) A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, lat.key0, lat.key1)) : 0u;
       lat.planes[g] = A0;
       lat.planes[plane + g] = A1;
-      if (D == 3) {
-        const uint32_t e2 = eq_bits(rb.a, rb.az) & vmask;
-        A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, lat.key0, lat.key1)) : 0u;
-        lat.planes[2 * plane + g] = A2;
-      }
+      if (D == 3) lat.planes[2 * plane + g] = A2;
     }
     X = A0 & (vmask >> 1);          // x-bonds whose +x site is in the same word
     S = ~(X << 1) & vmask;          // x-run starts
@@ -202,6 +248,16 @@ __global__ void __launch_bounds__(kTileThreads) k_label(Lattice lat, uint32_t sw
     const uint32_t draw = draws ? (uint32_t)sdraw[t] : 0u;
     lat.forest[i] = (gidx << shift) | (lr == t ? lr_bit : 0u) | draw;
   }
+  if (MEASURE) {
+    if (MM == 2) {
+      __syncthreads();
+      for (int k = threadIdx.x; k < kSmallQ; k += kTileThreads)
+        for (int w = 0; w < NW; ++w) s_hist[k] += s_whist[w * kSmallQ + k];
+      __syncthreads();
+      add_histogram(lat, mb, s_hist);
+    }
+    add_integer_sums<NW>(mb, (long long)m_acc, (long long)e_acc, s_red);
+  }
 }
 
 // ---------------------------------------------------------------- XY bonds
@@ -266,12 +322,27 @@ void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz) {
 
 cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
+  const Measure none{};
   if (lat.dim == 2) {
-    if (from_mask) k_label<2, true><<<g, kTileThreads, 0, st>>>(lat, sweep);
-    else k_label<2, false><<<g, kTileThreads, 0, st>>>(lat, sweep);
+    if (from_mask) k_label<2, true, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
+    else k_label<2, false, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
   } else {
-    if (from_mask) k_label<3, true><<<g, kTileThreads, 0, st>>>(lat, sweep);
-    else k_label<3, false><<<g, kTileThreads, 0, st>>>(lat, sweep);
+    if (from_mask) k_label<3, true, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
+    else k_label<3, false, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Measure& m,
+                                  cudaStream_t st) {
+  const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
+  const bool potts = lat.model == kPotts;
+  if (lat.dim == 2) {
+    if (potts) k_label<2, false, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
+    else k_label<2, false, 1><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
+  } else {
+    if (potts) k_label<3, false, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
+    else k_label<3, false, 1><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
   }
   return cudaGetLastError();
 }

@@ -84,6 +84,7 @@ int sw_label_from_bonds_noalloc(int dim, int L, const uint32_t* dev_mask, int32_
   lat.forest = scratch;
   lat.err = reinterpret_cast<int*>(scratch + SW_NOALLOC_MAX_SITES);
   lat.spins = nullptr;
+  lat.model = swgb::kIsing;
 
   int flag = 0;
   cudaError_t e = cudaMemsetAsync(lat.err, 0, sizeof(int), st);  // the flag must start at zero

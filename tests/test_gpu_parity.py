@@ -86,6 +86,38 @@ def test_potts_sweeps_bit_exact(sw, dim, L, q, T):
     run_exact_parity(sw, POTTS, dim, L, q, T, seed=2000 + L, sweeps=12)
 
 
+@pytest.mark.parametrize("model,dim,L,q,T", [
+    (ISING, 3, 48, 2, 4.5115), (ISING, 2, 100, 2, 2.269185), (POTTS, 2, 64, 3, 0.994973),
+    (POTTS, 3, 20, 8, 1.3), (POTTS, 2, 40, 40, 0.5), (ISING, 3, 7, 2, 4.0)])
+def test_back_to_back_sweep_records(sw, model, dim, L, q, T):
+    """Records of consecutive measured sweeps (each one measured by the next
+    sweep's labeling kernel, the last by the stand-alone kernel), also
+    across a measured -> discarded -> measured sequence."""
+    h = sw.sw_create(model, dim, L, q, T, 77)
+    o = oracle.Oracle(model, dim, L, q, T, 77)
+    try:
+        sw.sw_sweep(h, 9)
+        sw.sw_discard(h, 2)
+        sw.sw_sweep(h, 4)
+        recs = []
+        for n, meas in [(9, True), (2, False), (4, True)]:
+            for _ in range(n):
+                o.sweep(1, measure=meas)
+                if meas:
+                    recs.append(o.last_record())
+        got = sw.sw_get_series(h, 1, 9) + sw.sw_get_series(h, 12, 4)
+        for g, r in zip(got, recs):
+            for f in record_key(model) + ("M2", "Ed"):
+                assert g[f] == r[f], (f, g["sweep"], g[f], r[f])
+        a, b = sw.sw_measure(h), o.take_acc()
+        for f in ("n_sweeps", "sum_M2", "sum_M4", "sum_E", "sum_E2", "sum_nclusters"):
+            assert a[f] == b[f], f
+        assert np.array_equal(sw.sw_get_spins(h), o.spins)
+    finally:
+        sw.sw_destroy(h)
+        o.close()
+
+
 def test_low_and_high_temperature_limits(sw):
     # T -> 0: one cluster per equal-spin domain; T -> infinity: no bonds
     run_exact_parity(sw, ISING, 2, 40, 2, 1e-3, seed=5, sweeps=4)
