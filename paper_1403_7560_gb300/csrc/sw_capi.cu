@@ -76,6 +76,8 @@ void release(sw_handle* h) {
   cudaFree(h->lat.spins);
   cudaFree(h->lat.planes);
   cudaFree(h->lat.forest);
+  cudaFree(h->lat.hooked);
+  cudaFree(h->lat.nhooked);
   cudaFree(h->d_labels);
   cudaFree(h->d_block);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -194,6 +196,8 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   lat.key1 = (uint32_t)(seed >> 32);
   lat.model = model;
   h->bond_words = (size_t)dim * lat.R * (size_t)lat.W;
+  const size_t ntiles = (size_t)lat.ntx * lat.nty * lat.ntz;
+  lat.hook_cap = swgb::merge_list_capacity(dim);
 
   cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { cuda_fail(e, "stream"); release(h); return nullptr; }
@@ -201,8 +205,9 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
 
   // small buffers, carved from one block: err, cluster counts, slot sums,
   // slot histograms, XY partials, accumulators, series ring
-  const size_t off_err = 0, off_ncl = 64, off_acc = 128;
-  const size_t off_sums = 256;
+  const size_t off_err = 0, off_acc = 64;
+  const size_t off_ncl = 128;
+  const size_t off_sums = off_ncl + 2 * 8 * (size_t)swgb::kSlots;
   const size_t off_hist = off_sums + 16 * (size_t)swgb::kSlots;
   const size_t off_pd = off_hist + 8 * 256 * (size_t)swgb::kSlots;
   const size_t off_series = off_pd + 3 * 8 * (size_t)swgb::kMeasureBlocks;
@@ -211,6 +216,8 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   if ((e = cudaMalloc(&lat.spins, h->spin_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&lat.planes, h->bond_words * 4)) != cudaSuccess ||
       (e = cudaMalloc(&lat.forest, (size_t)N * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&lat.hooked, ntiles * (size_t)lat.hook_cap * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&lat.nhooked, ntiles * 4)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_block, block_bytes)) != cudaSuccess) {
     fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,
          std::string("device allocation: ") + cudaGetErrorString(e));

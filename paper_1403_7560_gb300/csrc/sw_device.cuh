@@ -84,14 +84,18 @@ __device__ __forceinline__ uint32_t draw_value(uint32_t w, uint32_t q) {
   return (uint32_t)(((unsigned long long)w * q) >> 32);
 }
 
-// 32 equality bits of two 32-byte rows held as 8 little-endian words.
+// 32 equality bits of two 32-byte rows held as 8 little-endian words.  A
+// byte of x = a ^ b is zero iff bit 7 of ((x & 0x7f) + 0x7f) | x is clear
+// (no carry crosses a byte); the four flags are gathered into a nibble by
+// one multiplication (bits 7, 15, 23, 31 land on bits 28..31).
 __device__ __forceinline__ uint32_t eq_bits(const uint32_t* a, const uint32_t* b) {
   uint32_t m = 0u;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const uint32_t e = __vcmpeq4(a[k], b[k]);
-    const uint32_t nib = ((e >> 7) & 1u) | ((e >> 14) & 2u) | ((e >> 21) & 4u) | ((e >> 28) & 8u);
-    m |= nib << (4 * k);
+    const uint32_t x = a[k] ^ b[k];
+    const uint32_t nz = (((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u;
+    const uint32_t z = nz ^ 0x80808080u;          // bit 7 of each byte: byte equal
+    m |= ((z * 0x00204081u) >> 28) << (4 * k);
   }
   return m;
 }
@@ -180,23 +184,27 @@ __device__ __forceinline__ uint32_t gfind(uint32_t* f, uint32_t x, int shift, ui
   return x;
 }
 
-__device__ __forceinline__ void gunion(uint32_t* f, uint32_t a, uint32_t b, int sb, int* err) {
+// Joins the trees of a and b; returns the root that was hooked under the
+// other tree (each root is hooked at most once), or 0xffffffff if the two
+// were already one tree.
+__device__ __forceinline__ uint32_t gunion(uint32_t* f, uint32_t a, uint32_t b, int sb, int* err) {
   const int shift = sb + 1;
   const uint32_t marker = 1u << sb;
   for (int it = 0; it < (1 << 20); ++it) {
     a = gfind(f, a, shift, marker);
     b = gfind(f, b, shift, marker);
-    if (a == b) return;
+    if (a == b) return 0xffffffffu;
     if (a < b) {
       const uint32_t t = a;
       a = b;
       b = t;
     }
     const uint32_t old = atomicMin(&f[a], (b << shift) | marker);
-    if ((old >> shift) == a) return;
+    if ((old >> shift) == a) return a;
     a = old >> shift;
   }
   atomicExch(err, kErrTimeout);
+  return 0xffffffffu;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -302,10 +310,14 @@ __device__ __forceinline__ void finalize_record(const Lattice& lat, const Measur
     E = block_combine<NW>(warp_sum(c), s_ri);
     S2 = block_combine<NW>(warp_sum(g), s_ri);
   }
+  long long nc = 0;
+  unsigned long long* ncl_slots = mb.nclusters + kSlots * (sweep & 1u);
+  for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {
+    nc += (long long)__ldcg(&ncl_slots[k]);
+    ncl_slots[k] = 0ull;
+  }
+  const long long ncl = block_combine<NW>(warp_sum(nc), s_ri);
   if (threadIdx.x != 0) return;
-  unsigned long long* ncl_slot = mb.nclusters + (sweep & 1u);
-  const long long ncl = (long long)__ldcg(ncl_slot);
-  *ncl_slot = 0ull;
   double M2, Ed;
   if (lat.model == kIsing) {
     M2 = __dmul_rn((double)M, (double)M);

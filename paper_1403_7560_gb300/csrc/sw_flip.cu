@@ -10,11 +10,13 @@
 // k_merge: bonds that leave a tile join the local roots at their two ends
 //   with atomicMin hooking of the larger root under the smaller; a warp
 //   performs each distinct (root, root) pair once.
-// k_flip: per tile, every local root walks to its global root (the smallest
-//   site index of the cluster), takes that root's draw and stores
-//   (root, draw) in its own word; after a CTA barrier every site reads its
-//   local root's word and writes its new state (set at random for
-//   Ising/Potts, reflection about the mirror line for XY).
+// k_merge also lists, per tile, the roots it hooked under another tree.
+// k_compress: every listed root walks to its global root (the smallest site
+//   index of the cluster), takes that root's draw and stores (root, draw) in
+//   its own word.
+// k_apply: every site reads its local root's word (or its own) and writes
+//   its new state (set at random for Ising/Potts, reflection about the
+//   mirror line for XY); global roots are counted.
 // k_labels_out: canonical labels (walk to the root) for readout.
 #include "sw_device.cuh"
 
@@ -93,98 +95,88 @@ __global__ void __launch_bounds__(kTileThreads) k_merge(Lattice lat) {
   }
   __syncthreads();
   const int n = s_n;
-  for (int e = threadIdx.x; e < n; e += kTileThreads) gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err);
+  __syncthreads();
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  // every root this tile hooks goes to the tile's hooked list for k_compress
+  // (no list on the labeling-only paths)
+  uint32_t* hooked = lat.hooked ? lat.hooked + (size_t)blockIdx.x * (size_t)lat.hook_cap : nullptr;
+  for (int e = threadIdx.x; e < n; e += kTileThreads) {
+    const uint32_t h = gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err);
+    if (hooked && h != 0xffffffffu) hooked[atomicAdd(&s_n, 1)] = h;
+  }
+  __syncthreads();
+  if (hooked && threadIdx.x == 0) lat.nhooked[blockIdx.x] = (uint32_t)s_n;
 }
 
-constexpr int kFlipThreads = 256;
-constexpr int kFlipBatch = 8;  // rows whose loads and root walks advance together
+constexpr int kFlipThreads = 256, kFlipWarps = kFlipThreads / 32;
+constexpr int kFlipUnroll = 4;   // independent sites in flight per thread
+constexpr unsigned kFlipBlocks = 152u * 8u;
 
-template <int MODEL, int D>
-__global__ void __launch_bounds__(kFlipThreads) k_flip(Lattice lat, uint32_t sweep, Measure mb,
-                                                        bool count, uint32_t finalize) {
-  constexpr int TY = Tile<D>::TY, ROWS = Tile<D>::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
-  constexpr int B = kFlipBatch;
-  static_assert(RPW % B == 0, "rows per warp must be a multiple of the batch");
+// Every root the merge hooked under another tree (the tiles' hooked lists)
+// walks to its global root and stores (root, marker, root draw) in its own
+// word, so that every site is at most two loads away from its cluster's
+// draw.  Block 0 first writes the record of the previous measured sweep,
+// from the sums its successor's labeling kernel left behind.
+__global__ void __launch_bounds__(kFlipThreads) k_compress(Lattice lat, Measure mb, uint32_t finalize) {
+  __shared__ long long s_red[kFlipWarps];
+  __shared__ double s_rd[kFlipWarps];
+  if (finalize != 0u && blockIdx.x == 0) finalize_record<kFlipWarps>(lat, mb, finalize, s_red, s_rd);
+  const int sb = lat.sbits, shift = sb + 1;
+  const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
+  const uint32_t ntiles = (uint32_t)(lat.ntx * lat.nty * lat.ntz);
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t n = __ldcg(&lat.nhooked[t]);
+    const uint32_t* list = lat.hooked + (size_t)t * (size_t)lat.hook_cap;
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const uint32_t a = __ldcg(&list[e]);
+      uint32_t cur = a, v = __ldcg(&lat.forest[a]);
+      int it = 0;
+      for (; it < (1 << 22); ++it) {
+        const uint32_t p = v >> shift;
+        if (p == cur) break;
+        cur = p;
+        v = __ldcg(&lat.forest[cur]);
+      }
+      if (it == (1 << 22)) atomicExch(lat.err, kErrTimeout);
+      __stcg(&lat.forest[a], (cur << shift) | lr_bit | (v & dmask));
+    }
+  }
+}
+
+// Every site takes its cluster's draw from its own word (local roots, now
+// compressed) or its local root's word, and writes its new state.
+template <int MODEL>
+__global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sweep, Measure mb,
+                                                         bool count) {
   __shared__ float s_phi;
-  __shared__ long long s_red[NW];
-  __shared__ double s_rd[NW];
-  // the record of the previous measured sweep, from the sums its successor's
-  // labeling kernel left behind
-  if (finalize != 0u && blockIdx.x == 0) finalize_record<NW>(lat, mb, finalize, s_red, s_rd);
+  __shared__ long long s_red[kFlipWarps];
   if (MODEL == kXY) {
     if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
     __syncthreads();
   }
-  const TileCoord tc = tile_coord<D>(lat);
-  const int L = lat.L;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sb = lat.sbits, shift = sb + 1;
   const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
-  const int x = tc.x0 + lane;
+  const uint32_t stride = gridDim.x * blockDim.x;
   long long roots = 0;
-
-  // local roots walk to their global root and store (root, marker, draw);
-  // the loads and walks of B rows advance together
-#pragma unroll 1
-  for (int k0 = 0; k0 < RPW; k0 += B) {
-    uint32_t idx[B], cur[B], v[B];
-    bool pend[B];
+  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < lat.N; base += kFlipUnroll * stride) {
+    uint32_t v[kFlipUnroll];
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      const int rr = warp + NW * (k0 + k);
-      const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
-      const bool ok = x < L && y < L && (D == 2 || z < L);
-      idx[k] = ok ? (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z) : 0u;
-      v[k] = ok ? __ldcg(&lat.forest[idx[k]]) : 0u;
-      const bool lr = ok && (v[k] & lr_bit);
-      pend[k] = lr && (v[k] >> shift) != idx[k];
-      if (lr && !pend[k]) ++roots;
-      cur[k] = v[k] >> shift;
-    }
-    for (int it = 0; it < (1 << 22); ++it) {
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < B; ++k)
-        if (pend[k]) v[k] = __ldcg(&lat.forest[cur[k]]);
-#pragma unroll
-      for (int k = 0; k < B; ++k) {
-        if (!pend[k]) continue;
-        const uint32_t p = v[k] >> shift;
-        if (p == cur[k]) {
-          pend[k] = false;
-          __stcg(&lat.forest[idx[k]], (cur[k] << shift) | lr_bit | (v[k] & dmask));
-        } else {
-          cur[k] = p;
-          any = true;
-        }
-      }
-      if (!any) break;
-      if (it == (1 << 22) - 1) atomicExch(lat.err, kErrTimeout);
-    }
-  }
-  __syncthreads();
-
-  // every site: its cluster's draw from its local root's word
-#pragma unroll 1
-  for (int k0 = 0; k0 < RPW; k0 += B) {
-    uint32_t idx[B], v[B];
-    bool ok[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-      const int rr = warp + NW * (k0 + k);
-      const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
-      ok[k] = x < L && y < L && (D == 2 || z < L);
-      idx[k] = ok[k] ? (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z) : 0u;
-      v[k] = ok[k] ? __ldcg(&lat.forest[idx[k]]) : 0u;
+    for (int k = 0; k < kFlipUnroll; ++k) {
+      const uint32_t i = base + k * stride;
+      v[k] = (i < lat.N) ? __ldcg(&lat.forest[i]) : lr_bit;
     }
 #pragma unroll
-    for (int k = 0; k < B; ++k)
-      if (ok[k] && !(v[k] & lr_bit)) v[k] = __ldcg(&lat.forest[v[k] >> shift]);
+    for (int k = 0; k < kFlipUnroll; ++k) {
+      const uint32_t i = base + k * stride;
+      if (!(v[k] & lr_bit)) v[k] = __ldcg(&lat.forest[v[k] >> shift]);
+      else if (i < lat.N && (v[k] >> shift) == i) ++roots;  // a cluster's root
+    }
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (!ok[k]) continue;
+    for (int k = 0; k < kFlipUnroll; ++k) {
+      const uint32_t i = base + k * stride;
+      if (i >= lat.N) continue;
       const uint32_t draw = v[k] & dmask;
-      const uint32_t i = idx[k];
       if (MODEL == kIsing) {
         static_cast<int8_t*>(lat.spins)[i] = draw ? (int8_t)-1 : (int8_t)1;
       } else if (MODEL == kPotts) {
@@ -202,8 +194,9 @@ __global__ void __launch_bounds__(kFlipThreads) k_flip(Lattice lat, uint32_t swe
     }
   }
   if (count) {
-    const long long tot = block_combine<NW>(warp_sum(roots), s_red);
-    if (threadIdx.x == 0 && tot) atomicAdd(mb.nclusters + (sweep & 1u), (unsigned long long)tot);
+    const long long tot = block_combine<kFlipWarps>(warp_sum(roots), s_red);
+    if (threadIdx.x == 0 && tot)
+      atomicAdd(mb.nclusters + kSlots * (sweep & 1u) + (blockIdx.x % kSlots), (unsigned long long)tot);
   }
 }
 
@@ -224,6 +217,8 @@ __global__ void __launch_bounds__(256) k_labels_out(Lattice lat, int32_t* out) {
 
 }  // namespace
 
+int merge_list_capacity(int dim) { return dim == 2 ? MergeShape<2>::kMax : MergeShape<3>::kMax; }
+
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
   if (lat.dim == 2) k_merge<2><<<g, kTileThreads, 0, st>>>(lat);
@@ -233,16 +228,14 @@ cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
 
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
                         uint32_t finalize, cudaStream_t st) {
-  const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  if (lat.dim == 2) {
-    if (model == kIsing) k_flip<kIsing, 2><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
-    else if (model == kPotts) k_flip<kPotts, 2><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
-    else k_flip<kXY, 2><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
-  } else {
-    if (model == kIsing) k_flip<kIsing, 3><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
-    else if (model == kPotts) k_flip<kPotts, 3><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
-    else k_flip<kXY, 3><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count, finalize);
-  }
+  unsigned g = (lat.N + kFlipThreads * kFlipUnroll - 1) / (kFlipThreads * kFlipUnroll);
+  if (g > kFlipBlocks) g = kFlipBlocks;
+  if (g == 0) g = 1;
+  const unsigned ntiles = (unsigned)(lat.ntx * lat.nty * lat.ntz);
+  k_compress<<<ntiles < kFlipBlocks ? ntiles : kFlipBlocks, kFlipThreads, 0, st>>>(lat, m, finalize);
+  if (model == kIsing) k_apply<kIsing><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
+  else if (model == kPotts) k_apply<kPotts><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
+  else k_apply<kXY><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,9 @@ struct Lattice {
   float twoK;           // XY: 2/T as float
   uint32_t key0, key1;  // Philox key = seed
   int model;            // Model
+  uint32_t* hooked;     // per tile: roots hooked by the merge [ntiles * hook_cap]
+  uint32_t* nhooked;    // per tile: number of hooked roots [ntiles]
+  int hook_cap;         // capacity of a tile's hooked list
 };
 
 // Buffers of the moment reduction (the per-sweep record and accumulators).
@@ -35,7 +38,7 @@ struct Lattice {
 // one block of a later kernel in the same stream.
 constexpr int kSlots = 64;
 struct Measure {
-  unsigned long long* nclusters;  // roots counted by the flip kernel, [2] by sweep parity
+  unsigned long long* nclusters;  // roots counted by the flip kernel, [2][kSlots] by sweep parity
   unsigned long long* sums;       // [kSlots][2]: integer M, E (two's complement)
   unsigned long long* hist;       // [kSlots][256]: Potts histogram
   double* part_d;                 // XY per-block partials [3 * kMeasureBlocks]
@@ -62,6 +65,9 @@ constexpr int kTile3Z = 16;
 constexpr int kTileThreads = 256;
 
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
+// Bonds that leave one tile (its +x, +y, +z faces): the most roots one
+// tile's merge can hook.
+int merge_list_capacity(int dim);
 
 // Message returned by sw_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

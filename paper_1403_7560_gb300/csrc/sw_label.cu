@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t
   static_assert(ROWS == kTileThreads, "one thread per row word");
   static_assert(!(MEASURE && FROM_MASK), "measurement needs the spins");
   __shared__ uint32_t par[ROWS * 32];
-  __shared__ uint8_t sdraw[ROWS * 32];
+  // cluster draws of the tile: row r's bytes 4j..4j+3 in word j*(ROWS+1)+r
+  // (row-thread stores and lane reads both bank-conflict free)
+  __shared__ uint32_t sdraw[8 * (ROWS + 1)];
   __shared__ uint32_t sX[ROWS], sS[ROWS];
   // Potts histogram: per-warp bins for q <= kSmallQ, shared bins above
   __shared__ unsigned int s_hist[MM == 2 ? 256 : 1];
@@ -178,14 +180,22 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t
       const uint32_t i0 = row * (uint32_t)L + (uint32_t)tc.x0;
       uint32_t cached = 0xffffffffu;
       uint4 w = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll 4
-      for (int b = 0; b < nvalid; ++b) {
-        const uint32_t i = i0 + (uint32_t)b;
-        if ((i >> 2) != cached) {
-          cached = i >> 2;
-          w = philox(cached, sweep, kDraw, 0u, lat.key0, lat.key1);
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        uint32_t packed = 0u;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int b = 4 * j + t;
+          if (b < nvalid) {
+            const uint32_t i = i0 + (uint32_t)b;
+            if ((i >> 2) != cached) {
+              cached = i >> 2;
+              w = philox(cached, sweep, kDraw, 0u, lat.key0, lat.key1);
+            }
+            packed |= draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.q) << (8 * t);
+          }
         }
-        sdraw[32 * r + b] = (uint8_t)draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.q);
+        sdraw[j * (ROWS + 1) + r] = packed;
       }
     }
   }
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t
     const uint32_t gz = (uint32_t)tc.z0 + lrow / TY;
     const uint32_t gidx = gx + (uint32_t)L * (gy + (uint32_t)L * gz);
     const uint32_t i = (uint32_t)(tc.x0 + lane) + (uint32_t)L * ((uint32_t)yy + (uint32_t)L * (uint32_t)zz);
-    const uint32_t draw = draws ? (uint32_t)sdraw[t] : 0u;
+    const uint32_t draw = draws ? (sdraw[(lane >> 2) * (ROWS + 1) + rr] >> (8 * (lane & 3))) & 0xffu : 0u;
     lat.forest[i] = (gidx << shift) | (lr == t ? lr_bit : 0u) | draw;
   }
   if (MEASURE) {

@@ -85,6 +85,8 @@ int sw_label_from_bonds_noalloc(int dim, int L, const uint32_t* dev_mask, int32_
   lat.err = reinterpret_cast<int*>(scratch + SW_NOALLOC_MAX_SITES);
   lat.spins = nullptr;
   lat.model = swgb::kIsing;
+  lat.hooked = nullptr;   // labeling only: the merge keeps no hooked lists
+  lat.nhooked = nullptr;
 
   int flag = 0;
   cudaError_t e = cudaMemsetAsync(lat.err, 0, sizeof(int), st);  // the flag must start at zero
