@@ -53,6 +53,9 @@ WORKLOAD = {"workload": "3D Ising SW sweep, simple cubic L=256 periodic, K=0.221
 # The merge touches only tile faces and is given per face bond instead.
 KERNEL_BYTES_PER_SITE = {"bond_label": 1 + 3 / 8 + 4, "merge": None, "flip": 4 + 1, "measure": 1}
 PHASES = ["bond_label", "merge", "flip", "measure"]
+# kernels one measured sweep launches: k_label (bonds + tile labels + the
+# previous sweep's measurement), k_merge, k_compress, k_apply
+KERNELS_PER_SWEEP = 4
 # Reference bytes model: 10.75 B/site/sweep for 3D Ising (bond 1.375,
 # tile label 4.375, flip 5), independent of the schedule.
 B_REF = 10.75
@@ -68,47 +71,68 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons; only samples
+    taken between mark_start() and mark_stop() are kept."""
+
+    FIELDS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index: int):
         self.proc = None
-        self.index = index
+        self.t0 = self.t1 = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(index),
-                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)   # let the sampler start before the timed region
         except Exception:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
         except Exception:
             self.proc.kill()
             return None
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        return self.parse(out, self.t0, self.t1)
+
+    @classmethod
+    def parse(cls, out: str, t0, t1):
+        import datetime
+        sm, mx, reasons, n_all = [], [], set(), 0
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
+            n_all += 1
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, cmax = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[4:8]):
+            if t0 is not None and t1 is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
+                continue
+            sm.append(clk)
+            mx.append(cmax)
+            for name, v in zip(cls.FIELDS, parts[4:8]):
                 if v.lower().startswith("active"):
-                    reasons.add(n)
+                    reasons.add(name)
         if not sm:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": [],
+                    "note": f"no sample inside the timed region ({n_all} outside)"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
 
@@ -164,8 +188,8 @@ def cpu_baseline(sweeps: int = 4):
 
 
 def run_reference(args):
-    world, rank, _ = dist_setup()
-    if rank != 0:
+    # the oracle runs once, on rank 0; other ranks have nothing to do
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     # bounded sample: at most ~90 s of oracle sweeps in total
     t0 = time.perf_counter()
@@ -206,12 +230,14 @@ def run_gpu(args):
     clocks = Clocks(local)
     barrier(world)
     torch.cuda.synchronize()
+    clocks.mark_start()
     for k in range(args.steps):
         starts[k].record(stream)
         sw.sw_sweep(h, 1)
         ends[k].record(stream)
         flush.fill_(k & 0xff)
     torch.cuda.synchronize()
+    clocks.mark_stop()
     barrier(world)
     clk = clocks.stop()
     sw.sw_sync(h)
@@ -274,7 +300,7 @@ def run_gpu(args):
             "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
             "update_only": {"value": update_only, "unit": UNIT},
             "b_ref": {"bytes_per_site": B_REF, "GBps": value * B_REF, "frac": value * B_REF / peak},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": KERNELS_PER_SWEEP * args.steps,
             "clocks": clk,
             "e2e": e2e,
             "moments": {"U": moments["U"], "e_per_spin": moments["e_per_spin"],
@@ -292,7 +318,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=4)
