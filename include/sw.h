@@ -193,6 +193,41 @@ int sw_get_series(sw_handle* h, uint64_t first, size_t count, sw_record* host);
 size_t sw_series_capacity(void);
 
 /* ------------------------------------------------------------------------
+ * Ragged batches (serving): many Ising/Potts lattices of one dimension,
+ * each a normal handle with its own L, q, T, seed, buffers and accumulators,
+ * advanced together with one launch per phase over all their tiles; one
+ * sweep is captured in a CUDA graph and replayed.  Each lattice's trajectory
+ * is the same alone and in a batch (the random numbers are keyed by seed,
+ * sweep, site and purpose only).  The paper runs one lattice at a time; this
+ * is the throughput path for many small lattices.
+ *
+ * sw_batch_create(dim)     new empty batch for dim = 2 or 3 (NULL on error);
+ *                          it owns a non-blocking stream.
+ * sw_batch_add(b, h)       h joins b (Ising/Potts of the batch's dim, in no
+ *                          other batch); the handle stays owned by the caller.
+ * sw_batch_remove(b, h)    h leaves b (synchronises the batch stream).
+ * sw_batch_sweep(b, n)     n measured sweeps of every member (enqueued);
+ *                          afterwards each member's counter has advanced by n
+ *                          and its records and accumulators are read with the
+ *                          usual per-handle calls, which wait for the batch.
+ * sw_batch_set_stream      run on a caller's non-default stream instead.
+ * sw_batch_size            number of members.
+ * sw_batch_destroy(b)      frees the batch (not its members).  sw_destroy of a
+ *                          member removes it from its batch first.
+ * sw_device_bytes          device bytes sw_create would allocate for a lattice
+ *                          (0 for invalid arguments): the budget a serving
+ *                          loop admits jobs against. */
+typedef struct sw_batch sw_batch;
+sw_batch* sw_batch_create(int dim);
+void sw_batch_destroy(sw_batch* b);
+int sw_batch_add(sw_batch* b, sw_handle* h);
+int sw_batch_remove(sw_batch* b, sw_handle* h);
+int sw_batch_sweep(sw_batch* b, int n);
+int sw_batch_set_stream(sw_batch* b, void* stream);
+size_t sw_batch_size(sw_batch* b);
+size_t sw_device_bytes(int model, int dim, int L, int q);
+
+/* ------------------------------------------------------------------------
  * Labeling without device allocation.  The paper has no counterpart: this
  * serves callers that may not allocate device memory themselves, such as a
  * plugin inside a host framework that owns every device byte through its

@@ -36,22 +36,28 @@ constexpr int kSeriesCap = 4096;
 
 }  // namespace
 
-struct sw_handle {
-  int model = 0, dim = 0, L = 0, q = 2;
-  double T = 0.0;
-  uint64_t seed = 0;
-  uint64_t sweep = 0;
-  size_t spin_bytes = 0, bond_words = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  Lattice lat{};
-  Measure meas{};
-  uint64_t pending = 0;         // measured sweep whose record is not yet written
-  int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
-  void* d_block = nullptr;      // one allocation holding every small buffer
-};
 
 namespace {
+
+// Offsets of the small per-handle buffers inside one allocation: error
+// flag, accumulators, cluster counts [2][kSlots], slot sums [kSlots][2],
+// slot histograms [kSlots][256], XY partials, series ring.
+struct BlockLayout {
+  size_t err, acc, ncl, sums, hist, pd, series, total;
+};
+
+BlockLayout block_layout() {
+  BlockLayout b;
+  b.err = 0;
+  b.acc = 64;
+  b.ncl = 128;
+  b.sums = b.ncl + 2 * 8 * (size_t)swgb::kSlots;
+  b.hist = b.sums + 16 * (size_t)swgb::kSlots;
+  b.pd = b.hist + 8 * 256 * (size_t)swgb::kSlots;
+  b.series = b.pd + 3 * 8 * (size_t)swgb::kMeasureBlocks;
+  b.total = b.series + sizeof(swgb::Record) * (size_t)kSeriesCap;
+  return b;
+}
 
 // Bond probability (Sec. 2, step (1), sign restored): Ising
 // p = 1 - exp(-2/T); Potts (H = -sum(delta - 1)) p = 1 - exp(-1/T).  The
@@ -116,13 +122,20 @@ cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k, uint32_t* finalize) {
   return swgb::launch_label(h->lat, k, false, h->stream);
 }
 
+}  // namespace
+
+size_t swgb::handle_block_bytes() { return block_layout().total; }
+
 // Write the record of a pending measured sweep with the stand-alone kernel.
-cudaError_t flush_pending(sw_handle* h) {
+cudaError_t swgb::flush_pending(sw_handle* h) {
   if (!h->pending) return cudaSuccess;
   const uint32_t k = (uint32_t)h->pending;
   h->pending = 0;
   return swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
 }
+
+namespace {
+using swgb::flush_pending;
 
 // One sweep; Ising/Potts leave their measurement pending (it is taken from
 // the next sweep's labeling kernel or by flush_pending), XY measures at once.
@@ -203,15 +216,11 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   if (e != cudaSuccess) { cuda_fail(e, "stream"); release(h); return nullptr; }
   h->own_stream = true;
 
-  // small buffers, carved from one block: err, cluster counts, slot sums,
-  // slot histograms, XY partials, accumulators, series ring
-  const size_t off_err = 0, off_acc = 64;
-  const size_t off_ncl = 128;
-  const size_t off_sums = off_ncl + 2 * 8 * (size_t)swgb::kSlots;
-  const size_t off_hist = off_sums + 16 * (size_t)swgb::kSlots;
-  const size_t off_pd = off_hist + 8 * 256 * (size_t)swgb::kSlots;
-  const size_t off_series = off_pd + 3 * 8 * (size_t)swgb::kMeasureBlocks;
-  const size_t block_bytes = off_series + sizeof(swgb::Record) * (size_t)kSeriesCap;
+  // small buffers, carved from one block (layout in block_layout)
+  const BlockLayout bl = block_layout();
+  const size_t off_err = bl.err, off_acc = bl.acc, off_ncl = bl.ncl, off_sums = bl.sums;
+  const size_t off_hist = bl.hist, off_pd = bl.pd, off_series = bl.series;
+  const size_t block_bytes = bl.total;
 
   if ((e = cudaMalloc(&lat.spins, h->spin_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&lat.planes, h->bond_words * 4)) != cudaSuccess ||
@@ -251,6 +260,7 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
 
 void sw_destroy(sw_handle* h) {
   if (!h) return;
+  if (h->batch) sw_batch_remove(h->batch, h);
   if (h->stream) cudaStreamSynchronize(h->stream);
   release(h);
 }

@@ -124,8 +124,8 @@ struct TileCoord {
 };
 
 template <int D>
-__device__ __forceinline__ TileCoord tile_coord(const Lattice& lat) {
-  int b = blockIdx.x;
+__device__ __forceinline__ TileCoord tile_coord(const Lattice& lat, uint32_t tile) {
+  int b = (int)tile;
   TileCoord c;
   c.tx = b % lat.ntx;
   b /= lat.ntx;
@@ -240,24 +240,24 @@ __device__ __forceinline__ T block_combine(T warp_total, T* scratch) {
 }
 
 // ---------------------------------------------------------------- records
-// Add a block's integer M, E (any thread's share) into its slot; called by
-// all threads of the block.
+// Add a block's integer M, E (any thread's share) into slot slot_of % kSlots;
+// called by all threads of the block.
 template <int NW>
-__device__ __forceinline__ void add_integer_sums(const Measure& mb, long long m, long long e,
-                                                 long long* s_red) {
+__device__ __forceinline__ void add_integer_sums(const Measure& mb, uint32_t slot_of, long long m,
+                                                 long long e, long long* s_red) {
   const long long M = block_combine<NW>(warp_sum(m), s_red);
   const long long E = block_combine<NW>(warp_sum(e), s_red);
   if (threadIdx.x == 0) {
-    unsigned long long* slot = mb.sums + 2 * (blockIdx.x % kSlots);
+    unsigned long long* slot = mb.sums + 2 * (slot_of % kSlots);
     if (M) atomicAdd(&slot[0], (unsigned long long)M);
     if (E) atomicAdd(&slot[1], (unsigned long long)E);
   }
 }
 
 // Add a block's Potts histogram (shared bins) into its slot.
-__device__ __forceinline__ void add_histogram(const Lattice& lat, const Measure& mb,
+__device__ __forceinline__ void add_histogram(const Lattice& lat, const Measure& mb, uint32_t slot_of,
                                               const unsigned int* s_hist) {
-  unsigned long long* slot = mb.hist + 256 * (blockIdx.x % kSlots);
+  unsigned long long* slot = mb.hist + 256 * (slot_of % kSlots);
   for (int k = threadIdx.x; k < lat.q; k += blockDim.x)
     if (s_hist[k]) atomicAdd(&slot[k], (unsigned long long)s_hist[k]);
 }

@@ -33,12 +33,18 @@ struct MergeShape {
 };
 
 template <int D>
-__global__ void __launch_bounds__(kTileThreads) k_merge(Lattice lat) {
+struct MergeSmem {
+  uint2 list[MergeShape<D>::kMax];
+  int n;
+};
+
+template <int D>
+__device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, MergeSmem<D>& sm) {
   constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NC = MergeShape<D>::kPerThread;
-  __shared__ uint2 s_list[MergeShape<D>::kMax];
-  __shared__ int s_n;
-  const TileCoord tc = tile_coord<D>(lat);
+  uint2* s_list = sm.list;
+  int& s_n = sm.n;
+  const TileCoord tc = tile_coord<D>(lat, tile);
   const int L = lat.L;
   const int shift = lat.sbits + 1;
   const int nx = min(32, L - tc.x0), ny = min(TY, L - tc.y0), nz = (D == 3) ? min(TZ, L - tc.z0) : 1;
@@ -100,48 +106,77 @@ __global__ void __launch_bounds__(kTileThreads) k_merge(Lattice lat) {
   __syncthreads();
   // every root this tile hooks goes to the tile's hooked list for k_compress
   // (no list on the labeling-only paths)
-  uint32_t* hooked = lat.hooked ? lat.hooked + (size_t)blockIdx.x * (size_t)lat.hook_cap : nullptr;
+  uint32_t* hooked = lat.hooked ? lat.hooked + (size_t)tile * (size_t)lat.hook_cap : nullptr;
   for (int e = threadIdx.x; e < n; e += kTileThreads) {
     const uint32_t h = gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err);
     if (hooked && h != 0xffffffffu) hooked[atomicAdd(&s_n, 1)] = h;
   }
   __syncthreads();
-  if (hooked && threadIdx.x == 0) lat.nhooked[blockIdx.x] = (uint32_t)s_n;
+  if (hooked && threadIdx.x == 0) lat.nhooked[tile] = (uint32_t)s_n;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTileThreads, 4) k_merge(Lattice lat) {
+  __shared__ MergeSmem<D> sm;
+  merge_tile<D>(lat, blockIdx.x, sm);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTileThreads, 4) k_merge_batch(BatchView bv) {
+  __shared__ MergeSmem<D> sm;
+  const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
+  merge_tile<D>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
 }
 
 constexpr int kFlipThreads = 256, kFlipWarps = kFlipThreads / 32;
 constexpr int kFlipUnroll = 4;   // independent sites in flight per thread
 constexpr unsigned kFlipBlocks = 152u * 8u;
 
+// The roots one tile's merge hooked walk to their global root and store
+// (root, marker, root draw) in their own word.
+__device__ __forceinline__ void compress_tile(const Lattice& lat, uint32_t t) {
+  const int sb = lat.sbits, shift = sb + 1;
+  const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
+  const uint32_t n = __ldcg(&lat.nhooked[t]);
+  const uint32_t* list = lat.hooked + (size_t)t * (size_t)lat.hook_cap;
+  for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const uint32_t a = __ldcg(&list[e]);
+    uint32_t cur = a, v = __ldcg(&lat.forest[a]);
+    int it = 0;
+    for (; it < (1 << 22); ++it) {
+      const uint32_t p = v >> shift;
+      if (p == cur) break;
+      cur = p;
+      v = __ldcg(&lat.forest[cur]);
+    }
+    if (it == (1 << 22)) atomicExch(lat.err, kErrTimeout);
+    __stcg(&lat.forest[a], (cur << shift) | lr_bit | (v & dmask));
+  }
+}
+
 // Every root the merge hooked under another tree (the tiles' hooked lists)
 // walks to its global root and stores (root, marker, root draw) in its own
 // word, so that every site is at most two loads away from its cluster's
 // draw.  Block 0 first writes the record of the previous measured sweep,
 // from the sums its successor's labeling kernel left behind.
-__global__ void __launch_bounds__(kFlipThreads) k_compress(Lattice lat, Measure mb, uint32_t finalize) {
+__global__ void __launch_bounds__(kFlipThreads, 4) k_compress(Lattice lat, Measure mb, uint32_t finalize) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
   if (finalize != 0u && blockIdx.x == 0) finalize_record<kFlipWarps>(lat, mb, finalize, s_red, s_rd);
-  const int sb = lat.sbits, shift = sb + 1;
-  const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
   const uint32_t ntiles = (uint32_t)(lat.ntx * lat.nty * lat.ntz);
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t n = __ldcg(&lat.nhooked[t]);
-    const uint32_t* list = lat.hooked + (size_t)t * (size_t)lat.hook_cap;
-    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const uint32_t a = __ldcg(&list[e]);
-      uint32_t cur = a, v = __ldcg(&lat.forest[a]);
-      int it = 0;
-      for (; it < (1 << 22); ++it) {
-        const uint32_t p = v >> shift;
-        if (p == cur) break;
-        cur = p;
-        v = __ldcg(&lat.forest[cur]);
-      }
-      if (it == (1 << 22)) atomicExch(lat.err, kErrTimeout);
-      __stcg(&lat.forest[a], (cur << shift) | lr_bit | (v & dmask));
-    }
-  }
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) compress_tile(lat, t);
+}
+
+// Batch: one CTA per member tile; the CTA of each member's tile 0 first
+// writes that member's previous record (every step after the first).
+__global__ void __launch_bounds__(kFlipThreads, 4) k_compress_batch(BatchView bv) {
+  __shared__ long long s_red[kFlipWarps];
+  __shared__ double s_rd[kFlipWarps];
+  const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
+  const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
+  const uint32_t step = *bv.step;
+  if (tile == 0u && step > 0u) finalize_record<kFlipWarps>(m.lat, m.meas, m.sweep0 + step, s_red, s_rd);
+  compress_tile(m.lat, tile);
 }
 
 // Every site takes its cluster's draw from its own word (local roots, now
@@ -200,6 +235,55 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
   }
 }
 
+// Batch apply: one CTA per member tile, warps over the tile's rows, lanes
+// over x; the member's model picks the state update.
+template <int D>
+__global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
+  constexpr int TY = Tile<D>::TY, ROWS = Tile<D>::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
+  constexpr int B = 8;
+  __shared__ long long s_red[NW];
+  const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
+  const Lattice& lat = m.lat;
+  const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
+  const uint32_t sweep = m.sweep0 + *bv.step + 1u;
+  const TileCoord tc = tile_coord<D>(lat, tile);
+  const int L = lat.L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sb = lat.sbits, shift = sb + 1;
+  const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
+  const int x = tc.x0 + lane;
+  long long roots = 0;
+#pragma unroll 1
+  for (int k0 = 0; k0 < RPW; k0 += B) {
+    uint32_t idx[B], v[B];
+    bool ok[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int rr = warp + NW * (k0 + k);
+      const int y = tc.y0 + rr % TY, z = tc.z0 + rr / TY;
+      ok[k] = x < L && y < L && (D == 2 || z < L);
+      idx[k] = ok[k] ? (uint32_t)x + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z) : 0u;
+      v[k] = ok[k] ? __ldcg(&lat.forest[idx[k]]) : lr_bit;
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (!(v[k] & lr_bit)) v[k] = __ldcg(&lat.forest[v[k] >> shift]);
+      else if (ok[k] && (v[k] >> shift) == idx[k]) ++roots;
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (!ok[k]) continue;
+      const uint32_t draw = v[k] & dmask;
+      if (lat.model == kIsing) static_cast<int8_t*>(lat.spins)[idx[k]] = draw ? (int8_t)-1 : (int8_t)1;
+      else static_cast<uint8_t*>(lat.spins)[idx[k]] = (uint8_t)draw;
+    }
+  }
+  const long long tot = block_combine<NW>(warp_sum(roots), s_red);
+  if (threadIdx.x == 0 && tot)
+    atomicAdd(m.meas.nclusters + kSlots * (sweep & 1u) + (tile % kSlots), (unsigned long long)tot);
+}
+
+__global__ void k_advance(uint32_t* step) { *step += 1u; }
+
 __global__ void __launch_bounds__(256) k_labels_out(Lattice lat, int32_t* out) {
   const int shift = lat.sbits + 1;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < lat.N; i += gridDim.x * blockDim.x) {
@@ -236,6 +320,20 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
   if (model == kIsing) k_apply<kIsing><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   else if (model == kPotts) k_apply<kPotts><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   else k_apply<kXY><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
+  if (dim == 2) k_merge_batch<2><<<ntiles, kTileThreads, 0, st>>>(bv);
+  else k_merge_batch<3><<<ntiles, kTileThreads, 0, st>>>(bv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
+  k_compress_batch<<<ntiles, kFlipThreads, 0, st>>>(bv);
+  if (dim == 2) k_apply_batch<2><<<ntiles, kFlipThreads, 0, st>>>(bv);
+  else k_apply_batch<3><<<ntiles, kFlipThreads, 0, st>>>(bv);
+  k_advance<<<1, 1, 0, st>>>(bv.step);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,9 @@
 
 #include <string>
 
+struct sw_handle;
+struct sw_batch;
+
 namespace swgb {
 
 enum Model { kIsing = 0, kPotts = 1, kXY = 2 };
@@ -46,6 +49,25 @@ struct Measure {
   double* acc;                    // n, sum M2, M4, E, E2, nclusters
   void* series;                   // sw_record ring
   int series_cap;
+};
+
+// One lattice of a batch: its device view, measurement buffers and the
+// sweep counter before the current batch call.
+struct BatchMember {
+  Lattice lat;
+  Measure meas;
+  uint32_t sweep0;
+};
+
+// Device-side description of a batch: members, the tile -> (member, tile)
+// map of one launch over every member's tiles, and the step counter of the
+// current batch call (advanced on the device after every sweep, so that a
+// captured sweep can be replayed).
+struct BatchView {
+  const BatchMember* members;
+  const uint32_t* tile_lattice;
+  const uint32_t* tile_index;
+  uint32_t* step;
 };
 
 // Record layout written by the measurement kernel (mirrors sw_record).
@@ -94,4 +116,33 @@ cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const 
                            cudaStream_t st);
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);
 
+// Batched phases: one launch over every tile of every member (Ising/Potts,
+// one dimension), then the step counter advances.
+cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
+cudaError_t launch_merge_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
+cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
+
+// Write the record of a pending measured sweep of h (stand-alone kernel).
+cudaError_t flush_pending(struct ::sw_handle* h);
+// Bytes of the small per-handle buffers (records, sums, accumulators).
+size_t handle_block_bytes();
+
 }  // namespace swgb
+
+// One lattice and everything the library allocated for it (include/sw.h:
+// sw_handle).
+struct sw_handle {
+  int model = 0, dim = 0, L = 0, q = 2;
+  double T = 0.0;
+  uint64_t seed = 0;
+  uint64_t sweep = 0;
+  size_t spin_bytes = 0, bond_words = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  swgb::Lattice lat{};
+  swgb::Measure meas{};
+  uint64_t pending = 0;         // measured sweep whose record is not yet written
+  int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
+  void* d_block = nullptr;      // one allocation holding every small buffer
+  struct sw_batch* batch = nullptr;  // batch the lattice belongs to, if any
+};

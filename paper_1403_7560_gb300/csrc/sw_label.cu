@@ -80,22 +80,36 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
 // spins (the state after sweep - 1): M and E from the row words' equality
 // masks and the Potts histogram, added to the measurement slots (the flip
 // kernel of this sweep writes the record of sweep - 1).  MM = 0: none.
+// Shared memory of one tile's labeling.
+template <int D>
+struct LabelSmem {
+  static constexpr int ROWS = Tile<D>::ROWS, NW = kTileThreads / 32;
+  uint32_t par[ROWS * 32];
+  // cluster draws of the tile: row r's bytes 4j..4j+3 in word j*(ROWS+1)+r
+  // (row-thread stores and lane reads both bank-conflict free)
+  uint32_t sdraw[8 * (ROWS + 1)];
+  uint32_t sX[ROWS], sS[ROWS];
+  // Potts histogram: per-warp bins for q <= kSmallQ, shared bins above
+  unsigned int s_hist[256];
+  unsigned int s_whist[NW * kSmallQ];
+  long long s_red[NW];
+};
+
 template <int D, bool FROM_MASK, int MM>
-__global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t sweep, Measure mb) {
+__device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, uint32_t sweep,
+                                           const Measure& mb, LabelSmem<D>& sm) {
   constexpr bool MEASURE = MM != 0;
   constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ, ROWS = Tile<D>::ROWS;
   constexpr int NW = kTileThreads / 32, RPW = ROWS / NW;
   static_assert(ROWS == kTileThreads, "one thread per row word");
   static_assert(!(MEASURE && FROM_MASK), "measurement needs the spins");
-  __shared__ uint32_t par[ROWS * 32];
-  // cluster draws of the tile: row r's bytes 4j..4j+3 in word j*(ROWS+1)+r
-  // (row-thread stores and lane reads both bank-conflict free)
-  __shared__ uint32_t sdraw[8 * (ROWS + 1)];
-  __shared__ uint32_t sX[ROWS], sS[ROWS];
-  // Potts histogram: per-warp bins for q <= kSmallQ, shared bins above
-  __shared__ unsigned int s_hist[MM == 2 ? 256 : 1];
-  __shared__ unsigned int s_whist[MM == 2 ? NW * kSmallQ : 1];
-  __shared__ long long s_red[NW];
+  uint32_t* par = sm.par;
+  uint32_t* sdraw = sm.sdraw;
+  uint32_t* sX = sm.sX;
+  uint32_t* sS = sm.sS;
+  unsigned int* s_hist = sm.s_hist;
+  unsigned int* s_whist = sm.s_whist;
+  long long* s_red = sm.s_red;
   int m_acc = 0, e_acc = 0;
   if (MM == 2) {
     for (int k = threadIdx.x; k < 256; k += kTileThreads) s_hist[k] = 0u;
@@ -103,7 +117,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t
     __syncthreads();
   }
 
-  const TileCoord tc = tile_coord<D>(lat);
+  const TileCoord tc = tile_coord<D>(lat, tile);
   const int L = lat.L;
   const uint32_t plane = lat.R * (uint32_t)lat.W;
   const int nvalid = min(32, L - tc.x0);
@@ -264,10 +278,32 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t
       for (int k = threadIdx.x; k < kSmallQ; k += kTileThreads)
         for (int w = 0; w < NW; ++w) s_hist[k] += s_whist[w * kSmallQ + k];
       __syncthreads();
-      add_histogram(lat, mb, s_hist);
+      add_histogram(lat, mb, tile, s_hist);
     }
-    add_integer_sums<NW>(mb, (long long)m_acc, (long long)e_acc, s_red);
+    add_integer_sums<NW>(mb, tile, (long long)m_acc, (long long)e_acc, s_red);
   }
+}
+
+template <int D, bool FROM_MASK, int MM>
+__global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t sweep, Measure mb) {
+  __shared__ LabelSmem<D> sm;
+  label_tile<D, FROM_MASK, MM>(lat, blockIdx.x, sweep, mb, sm);
+}
+
+// Ising/Potts lattices of a batch, one tile per CTA; sweep numbers come from
+// the batch step counter, and every step after the first also measures the
+// incoming state of its lattice (the record of the previous sweep).
+template <int D>
+__global__ void __launch_bounds__(kTileThreads, 4) k_label_batch(BatchView bv) {
+  __shared__ LabelSmem<D> sm;
+  const uint32_t b = __ldg(&bv.tile_lattice[blockIdx.x]);
+  const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
+  const BatchMember& m = bv.members[b];
+  const uint32_t step = *bv.step;
+  const uint32_t sweep = m.sweep0 + step + 1u;
+  if (step == 0u) label_tile<D, false, 0>(m.lat, tile, sweep, m.meas, sm);
+  else if (m.lat.model == kPotts) label_tile<D, false, 2>(m.lat, tile, sweep, m.meas, sm);
+  else label_tile<D, false, 1>(m.lat, tile, sweep, m.meas, sm);
 }
 
 // ---------------------------------------------------------------- XY bonds
@@ -340,6 +376,12 @@ cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cud
     if (from_mask) k_label<3, true, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
     else k_label<3, false, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
+  if (dim == 2) k_label_batch<2><<<ntiles, kTileThreads, 0, st>>>(bv);
+  else k_label_batch<3><<<ntiles, kTileThreads, 0, st>>>(bv);
   return cudaGetLastError();
 }
 

@@ -87,10 +87,10 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
   }
   if (MODEL == kPotts) {
     __syncthreads();
-    add_histogram(lat, mb, s_hist);
+    add_histogram(lat, mb, blockIdx.x, s_hist);
   }
   if (MODEL != kXY) {
-    add_integer_sums<kMWarps>(mb, m, e, s_ri);
+    add_integer_sums<kMWarps>(mb, blockIdx.x, m, e, s_ri);
     return;
   }
   // XY: float within a warp, double across warps; per-block partials are

@@ -66,6 +66,14 @@ _SIGNATURES = {
     "sw_series_capacity": (_sz, []),
     "sw_sweep_timed": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
     "sw_label_from_bonds_noalloc": (_i, [_i, _i, _vp, _vp, _vp]),
+    "sw_batch_create": (_vp, [_i]),
+    "sw_batch_destroy": (None, [_vp]),
+    "sw_batch_add": (_i, [_vp, _vp]),
+    "sw_batch_remove": (_i, [_vp, _vp]),
+    "sw_batch_sweep": (_i, [_vp, _i]),
+    "sw_batch_set_stream": (_i, [_vp, _vp]),
+    "sw_batch_size": (_sz, [_vp]),
+    "sw_device_bytes": (_sz, [_i, _i, _i, _i]),
 }
 
 SW_NOALLOC_MAX_SITES = 1 << 21
@@ -237,3 +245,51 @@ def sw_label_from_bonds_noalloc(dim: int, L: int, dev_mask: int, dev_labels: int
 
 def sw_series_capacity() -> int:
     return int(lib().sw_series_capacity())
+
+
+class Batch:
+    """An sw_batch* (ragged batch of Ising/Potts lattices of one dimension)."""
+
+    def __init__(self, ptr: int, dim: int):
+        self.ptr, self.dim = ptr, dim
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.ptr)
+
+
+def sw_batch_create(dim: int) -> Batch:
+    ptr = lib().sw_batch_create(dim)
+    if not ptr:
+        raise SwError(SW_ERR_BAD_ARG, sw_last_error())
+    return Batch(ptr, dim)
+
+
+def sw_batch_destroy(b: Batch):
+    if b is not None and b.ptr:
+        lib().sw_batch_destroy(b)
+        b.ptr = 0
+
+
+def sw_batch_add(b: Batch, h: Handle):
+    _check(lib().sw_batch_add(b, h))
+
+
+def sw_batch_remove(b: Batch, h: Handle):
+    _check(lib().sw_batch_remove(b, h))
+
+
+def sw_batch_sweep(b: Batch, n: int):
+    _check(lib().sw_batch_sweep(b, n))
+
+
+def sw_batch_set_stream(b: Batch, stream: int):
+    _check(lib().sw_batch_set_stream(b, ctypes.c_void_p(stream)))
+
+
+def sw_batch_size(b: Batch) -> int:
+    return int(lib().sw_batch_size(b))
+
+
+def sw_device_bytes(model: int, dim: int, L: int, q: int) -> int:
+    return int(lib().sw_device_bytes(model, dim, L, q))
