@@ -315,6 +315,118 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def _job_list(specs):
+    from paper_1403_7560_gb300.serve import Job
+    return [Job(**d) for d in specs]
+
+
+def run_batch(args):
+    """Ragged batch of 256 2D Ising/Potts lattices (seed 1003), advanced
+    together (one launch per phase, graph-replayed sweeps) vs the same
+    lattices swept one at a time.  Inputs total ~1 GB (larger than L2)."""
+    import torch
+    import inputs
+    from paper_1403_7560_gb300 import build, sw
+    build.build()
+    torch.cuda.set_device(0)
+    specs = inputs.ragged_batch(256, 1003)
+    sites = sum(L ** d for (_, d, L, _, _, _) in specs)
+    st = torch.cuda.Stream()
+    hs = [sw.sw_create(m, d, L, q, T, seed) for (m, d, L, q, T, seed) in specs]
+    b = sw.sw_batch_create(2)
+    sw.sw_batch_set_stream(b, st.cuda_stream)
+    for h in hs:
+        sw.sw_set_stream(h, st.cuda_stream)
+        sw.sw_batch_add(b, h)
+    sw.sw_batch_sweep(b, max(args.warmup, 3))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.mark_start()
+    e0.record(st)
+    sw.sw_batch_sweep(b, args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks.mark_stop()
+    clk = clocks.stop()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    sw.sw_batch_destroy(b)
+    # the plain path: each lattice alone, one after another, same sweeps
+    k_serial = min(args.steps, 50)
+    e0.record(st)
+    for h in hs:
+        sw.sw_sweep(h, k_serial)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_serial = e0.elapsed_time(e1) / 1e3
+    for h in hs:
+        sw.sw_measure(h)
+        sw.sw_destroy(h)
+    v_batch = sites * args.steps / (t_batch * 1e9)
+    v_serial = sites * k_serial / (t_serial * 1e9)
+    line = {"metric": "ragged batch site-updates/ns (256 2D Ising/Potts lattices, L 32..1024)",
+            "value": v_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_batch / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic",
+            "config": {"workload": "ragged batch: 256 2D lattices, model uniform over Ising / Potts q=3 "
+                                   "/ Potts q=4, L uniform over {32,48,...,1024}, T in [0.8,1.2] Tc, "
+                                   "seed 1003, one measured sweep per step, CUDA-graph replay",
+                       "sites": sites, "l2": "inputs larger than L2"},
+            "serial": {"value": v_serial, "unit": UNIT, "steps": k_serial,
+                       "note": "each lattice alone with sw_sweep, one after another"},
+            "speedup_vs_serial": v_batch / v_serial,
+            "gpu_launches": 5 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Served request stream (seed 1004): continuous batching vs the
+    one-at-a-time plain path, at saturation (all queued at t = 0) and at
+    0.7 of the serial capacity (Poisson arrivals)."""
+    import torch
+    import inputs
+    from paper_1403_7560_gb300 import build, serve
+    build.build()
+    torch.cuda.set_device(0)
+    kw = dict(max_L2=args.max_l2, max_L3=args.max_l3, sweeps=(100, args.max_sweeps))
+    budget = int(args.budget_gb * (1 << 30))
+
+    def served(jobs, realtime):
+        srv = serve.Server(budget, chunk=args.chunk)
+        t0 = time.perf_counter()
+        done = srv.run(jobs, realtime=realtime)
+        wall = time.perf_counter() - t0
+        srv.close()
+        return serve.summary(done, wall)
+
+    def serial(jobs, realtime):
+        t0 = time.perf_counter()
+        done = serve.run_serial(jobs, realtime=realtime)
+        return serve.summary(done, time.perf_counter() - t0)
+
+    # warm-up: build the kernels' first launches
+    served(_job_list(inputs.served_stream(6, 7, **kw)), False)
+    sat_srv = served(_job_list(inputs.served_stream(args.jobs, 1004, **kw)), False)
+    sat_ser = serial(_job_list(inputs.served_stream(args.jobs, 1004, **kw)), False)
+    rate = 0.7 * sat_ser["jobs_per_s"]
+    lat_srv = served(_job_list(inputs.served_stream(args.jobs, 1004, rate=rate, **kw)), True)
+    lat_ser = serial(_job_list(inputs.served_stream(args.jobs, 1004, rate=rate, **kw)), True)
+    line = {"metric": "served mix jobs/s, p50/p99", "value": sat_srv["jobs_per_s"], "unit": "jobs/s",
+            "n_gpus": 1, "steps": args.jobs, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8/uint8/f32", "data": "synthetic",
+            "config": {"workload": f"served stream, seed 1004, {args.jobs} jobs, class uniform over "
+                                   "2D Ising / 3D Ising / 2D Potts q=3,4,8 / 3D XY, L log-uniform in "
+                                   f"[16,{args.max_l2}] (2D) or [16,{args.max_l3}] (3D), T = Tc(1+U(-0.02,0.02)), "
+                                   f"sweeps log-uniform in [100,{args.max_sweeps}]",
+                       "budget_gb": args.budget_gb, "chunk": args.chunk},
+            "saturation": {"served": sat_srv, "serial": sat_ser,
+                           "speedup": sat_srv["jobs_per_s"] / sat_ser["jobs_per_s"]},
+            "latency_at_0.7_serial_capacity": {"rate_jobs_per_s": rate, "served": lat_srv,
+                                               "serial": lat_ser}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,9 +435,22 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="ising3d_L256", choices=["ising3d_L256", "batch", "serve"],
+                    help="the headline 3D Ising L=256 sweep (default), the ragged batch, or the "
+                         "served stream (one GPU)")
+    ap.add_argument("--jobs", type=int, default=48, help="serve: jobs in the stream")
+    ap.add_argument("--max-l2", type=int, default=1024, help="serve: largest 2D L")
+    ap.add_argument("--max-l3", type=int, default=128, help="serve: largest 3D L")
+    ap.add_argument("--max-sweeps", type=int, default=1000, help="serve: most sweeps of a job")
+    ap.add_argument("--budget-gb", type=float, default=32.0, help="serve: HBM budget")
+    ap.add_argument("--chunk", type=int, default=64, help="serve: sweeps per engine iteration")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -104,3 +104,57 @@ def spiral_mask(L: int) -> np.ndarray:
             y = min(ya, yb)
             bits[1, xa + L * y] = True
     return pack_planes(bits, 2, L)
+
+
+# ---------------------------------------------------------------- batch / serving
+TC_3D_ISING = 1.0 / K_3D_ISING      # 4.511524
+TC_3D_XY = 2.20184
+
+
+def ragged_batch(n: int = 256, seed: int = 1003):
+    """The ragged-batch workload: n 2D lattices, model uniform over
+    {Ising, Potts q=3, Potts q=4}, L uniform over {32, 48, ..., 1024},
+    T uniform in [0.8 Tc, 1.2 Tc], one seed per lattice.
+    Returns a list of (model, dim, L, q, T, seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        kind = int(rng.integers(0, 3))
+        model, q = (ISING, 2) if kind == 0 else (POTTS, 3 if kind == 1 else 4)
+        L = 16 * int(rng.integers(2, 65))
+        tc = TC_2D_ISING if model == ISING else tc_2d_potts(q)
+        T = tc * float(rng.uniform(0.8, 1.2))
+        out.append((model, 2, L, q, T, int(rng.integers(1, 2 ** 62))))
+    return out
+
+
+def served_stream(n: int, seed: int = 1004, rate: float | None = None, max_L2: int = 4096,
+                  max_L3: int = 256, sweeps=(100, 5000)):
+    """The served request stream: n jobs, class uniform over {2D Ising, 3D
+    Ising, 2D Potts q=3, 4, 8, 3D XY}, L log-uniform in [16, max_L2] (2D) or
+    [16, max_L3] (3D), T = Tc (1 + U(-0.02, 0.02)), sweeps log-uniform in
+    the given range, Poisson arrivals at `rate` jobs/s (all at t = 0 when
+    rate is None).  Returns dicts with the job fields."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    jobs = []
+    for k in range(n):
+        kind = int(rng.integers(0, 6))
+        if kind == 0:
+            model, dim, q, tc = ISING, 2, 2, TC_2D_ISING
+        elif kind == 1:
+            model, dim, q, tc = ISING, 3, 2, TC_3D_ISING
+        elif kind in (2, 3, 4):
+            q = (3, 4, 8)[kind - 2]
+            model, dim, tc = POTTS, 2, tc_2d_potts(q)
+        else:
+            model, dim, q, tc = XY, 3, 2, TC_3D_XY
+        hi = max_L2 if dim == 2 else max_L3
+        L = int(round(math.exp(rng.uniform(math.log(16), math.log(hi)))))
+        T = tc * (1.0 + float(rng.uniform(-0.02, 0.02)))
+        nsw = int(round(math.exp(rng.uniform(math.log(sweeps[0]), math.log(sweeps[1])))))
+        if rate:
+            t += float(rng.exponential(1.0 / rate))
+        jobs.append(dict(id=k, model=model, dim=dim, L=L, q=q, T=T,
+                         seed=int(rng.integers(1, 2 ** 62)), sweeps=nsw, arrival=t))
+    return jobs
