@@ -15,6 +15,7 @@
  *       SW_ISING  int8_t  +1 / -1
  *       SW_POTTS  uint8_t 0 .. q-1
  *       SW_XY     float   angle theta in [0, 2 pi)
+ *       SW_CLOCK  uint16  clock state p in [0, q), angle 2 pi p / q
  *   - Bond bit-planes: plane d (0 <= d < dim) holds bond (i, i + e_d); each
  *     row (fixed y, z) is padded to W = ceil(L/32) uint32 words; the bit of
  *     site i is word d*R*W + row*W + (x >> 5), bit (x & 31), with
@@ -33,6 +34,17 @@
  *       2 cluster draws: counter (i >> 2, sweep, 2, 0), word (i & 3) is
  *         the draw w of site i, used when i is the root of its cluster;
  *       3 XY mirror angle: counter (0, sweep, 3, 0), word 0.
+ *   - q-state clock model (the paper's discretised XY, Sec. 1 and Sec. 3,
+ *     q = 512 there): per sweep a mirror index s = floor(w 2q / 2^32) from
+ *     counter (0, sweep, 3, 0) word 0 picks the reflection p -> (s - p) mod q.
+ *     The Ising projection of site i is x_i = sin(pi k_i / q), k_i =
+ *     (2 p_i - s) mod 2q.  Bond (i,d) is active iff w_d < t[k_i][k_j], w_d =
+ *     word d of counter (i, sweep, 1, 0) and t[a][b] = floor(-expm1(-(2/T)
+ *     x_a x_b) 2^32) where x_a x_b > 0, else 0 (double, computed once per
+ *     lattice).  Clusters reflect when their root's draw w >= 2^31.  Moments
+ *     come from integer histograms of states and of bond differences
+ *     (p_i - p_j) mod q summed against cos/sin((2 pi k)/q) in index order,
+ *     so trajectories and moments are reproducible bit for bit.
  *   - Ownership: the handle owns every device buffer it allocates; host
  *     buffers passed in stay owned by the caller and are only read or
  *     written during the call (the call synchronises the handle's stream).
@@ -54,7 +66,7 @@
 extern "C" {
 #endif
 
-enum sw_model { SW_ISING = 0, SW_POTTS = 1, SW_XY = 2 };
+enum sw_model { SW_ISING = 0, SW_POTTS = 1, SW_XY = 2, SW_CLOCK = 3 };
 
 enum sw_status {
   SW_OK = 0,
@@ -70,9 +82,9 @@ typedef struct sw_handle sw_handle;
 /* Sums over the measured sweeps since the previous sw_measure (Sec. 2,
  * outputs of the sample program; Sec. 3, moment ratio U).
  *   M2 per sweep: Ising M^2 with M = sum s_i; Potts (q sum_k n_k^2 - N^2)/(q-1)
- *   (Sec. 2, Potts equation); XY (sum cos)^2 + (sum sin)^2.  M4 = (M2)^2.
- *   E per sweep: Ising -sum s_i s_j; Potts sum (1 - delta); XY
- *   -sum cos(theta_i - theta_j).
+ *   (Sec. 2, Potts equation); XY and clock (sum cos)^2 + (sum sin)^2.
+ *   M4 = (M2)^2.  E per sweep: Ising -sum s_i s_j; Potts sum (1 - delta);
+ *   XY and clock -sum cos(theta_i - theta_j).
  *   U = <M4>/<M2>^2;  e_per_spin = <E>/N;  c_per_spin = (<E^2>-<E>^2)/(N T^2);
  *   mean_cluster_size = N / <number of clusters>. */
 typedef struct sw_moments {
@@ -106,7 +118,8 @@ typedef struct sw_record {
 
 /* Create a lattice (paper: device_function_spinset + the parameters nx,
  * mcs1/mcs2 of Sec. 2).  model: sw_model; dim: 2 or 3; L >= 4; q: Potts
- * states 2..256 (ignored otherwise); T > 0 in units of J; seed: Philox key.
+ * states 2..256 or clock states 2..1024 (ignored otherwise); T > 0 in units
+ * of J; seed: Philox key.
  * The initial state is random from the seed (sweep counter 0).  Returns NULL
  * on a bad argument, an oversized lattice (N * 2^(b+1) must fit in 32 bits,
  * b = bits of the cluster draw: 1 for Ising/XY, ceil(log2 q) for Potts) or

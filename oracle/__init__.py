@@ -20,7 +20,7 @@ import threading
 
 import numpy as np
 
-ISING, POTTS, XY = 0, 1, 2
+ISING, POTTS, XY, CLOCK = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sw_oracle.c")
@@ -96,6 +96,11 @@ def lib():
             L.oracle_set_sweep_counter.argtypes = [vp, ctypes.c_uint32]
             L.oracle_last_record.argtypes = [vp, ctypes.POINTER(Record)]
             L.oracle_take_acc.argtypes = [vp, ctypes.POINTER(Acc)]
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.oracle_clock_trig.argtypes = [ctypes.c_int, dp, dp]
+            L.oracle_clock_thresholds.argtypes = [ctypes.c_int, ctypes.c_double, u32p]
+            L.oracle_clock_mirror.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int]
+            L.oracle_clock_mirror.restype = ctypes.c_uint32
             _lib = L
     return _lib
 
@@ -109,7 +114,7 @@ def _i32p(a):
 
 
 def spin_dtype(model: int):
-    return {ISING: np.int8, POTTS: np.uint8, XY: np.float32}[model]
+    return {ISING: np.int8, POTTS: np.uint8, XY: np.float32, CLOCK: np.uint16}[model]
 
 
 def n_sites(dim: int, L: int) -> int:
@@ -137,6 +142,24 @@ def bond_threshold(model: int, T: float) -> int:
 
 def xy_phi(seed: int, sweep: int) -> np.float32:
     return np.float32(lib().oracle_xy_phi(seed, sweep))
+
+
+def clock_trig(q: int):
+    c = np.zeros(q, dtype=np.float64)
+    s = np.zeros(q, dtype=np.float64)
+    lib().oracle_clock_trig(q, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return c, s
+
+
+def clock_thresholds(q: int, T: float) -> np.ndarray:
+    t = np.zeros((2 * q, 2 * q), dtype=np.uint32)
+    lib().oracle_clock_thresholds(q, T, _u32p(t))
+    return t
+
+
+def clock_mirror(seed: int, sweep: int, q: int) -> int:
+    return int(lib().oracle_clock_mirror(seed, sweep, q))
 
 
 def init_spins(model, dim, L, q, seed) -> np.ndarray:

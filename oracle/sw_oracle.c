@@ -39,8 +39,20 @@
  *                      XY: counter (i, k, 1, 0), word d -> u(i,d).
  *   purpose 2 (DRAW):  counter (i >> 2, k, 2, 0), word (i & 3) -> the
  *                      cluster draw w(i), used when i is a cluster root.
- *   purpose 3 (AXIS):  counter (0, k, 3, 0), word 0 -> XY mirror angle.
+ *   purpose 3 (AXIS):  counter (0, k, 3, 0), word 0 -> XY mirror angle, or
+ *                      the clock model's mirror index.
+ *   Clock bonds:       counter (i, k, 1, 0), word d -> u(i,d) (32 bits).
  * (k is the sweep number, starting at 1; the initial state uses 0.)
+ *
+ * q-state clock model (the paper's discretised XY, theta_p = 2 pi p / q,
+ * q = 512 in Sec. 3): spins p in [0, q) as uint16.  Per sweep a mirror
+ * index s = floor(w q2 / 2^32), q2 = 2q, picks the reflection p -> (s - p)
+ * mod q (the mirror line at angle pi s / q); the Ising projection of site i
+ * is x_i = sin(pi k_i / q) with k_i = (2 p_i - s) mod 2q.  Bond (i,d) is
+ * active iff x_i x_j > 0 and u(i,d) < t[k_i][k_j], t = floor((1 - exp(-2K
+ * x_a x_b)) 2^32) from a table evaluated in double.  Moments come from the
+ * integer histograms of states and of bond differences (p_i - p_j) mod q,
+ * summed against cos/sin tables in index order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,6 +62,7 @@
 #define OR_ISING 0
 #define OR_POTTS 1
 #define OR_XY 2
+#define OR_CLOCK 3
 
 #define PURPOSE_INIT 0u
 #define PURPOSE_BOND 1u
@@ -157,6 +170,61 @@ float oracle_xy_phi(uint64_t seed, uint32_t sweep) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Clock model tables.  Angle of state p: (2 pi p) / q in double; the
+ * projection table x(k) = sin((pi k) / q) for k in [0, 2q); the threshold
+ * table t[a][b] = floor(-expm1(-(2/T) x(a) x(b)) 2^32) where x(a) x(b) > 0,
+ * else 0. */
+static const double OR_PI = 3.141592653589793238463;
+
+void oracle_clock_trig(int q, double* cosv, double* sinv) {
+  for (int p = 0; p < q; ++p) {
+    const double a = (2.0 * OR_PI * (double)p) / (double)q;
+    cosv[p] = cos(a);
+    sinv[p] = sin(a);
+  }
+}
+
+void oracle_clock_thresholds(int q, double T, uint32_t* t) {
+  const int q2 = 2 * q;
+  double* x = (double*)malloc(sizeof(double) * (size_t)q2);
+  for (int k = 0; k < q2; ++k) x[k] = sin((OR_PI * (double)k) / (double)q);
+  const double twoK = 2.0 / T;
+  for (int a = 0; a < q2; ++a)
+    for (int b = 0; b < q2; ++b) {
+      const double prod = x[a] * x[b];
+      uint32_t v = 0u;
+      if (prod > 0.0) {
+        double f = floor(-expm1(-(twoK * prod)) * 4294967296.0);
+        if (f > 4294967295.0) f = 4294967295.0;
+        v = (uint32_t)f;
+      }
+      t[(size_t)a * (size_t)q2 + (size_t)b] = v;
+    }
+  free(x);
+}
+
+/* The threshold table of the last (q, T) asked for, kept between sweeps. */
+static const uint32_t* clock_table(int q, double T) {
+  static uint32_t* tab = NULL;
+  static int tab_q = 0;
+  static double tab_T = 0.0;
+  if (!tab || tab_q != q || tab_T != T) {
+    free(tab);
+    tab = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(2 * q) * (size_t)(2 * q));
+    oracle_clock_thresholds(q, T, tab);
+    tab_q = q;
+    tab_T = T;
+  }
+  return tab;
+}
+
+uint32_t oracle_clock_mirror(uint64_t seed, uint32_t sweep, int q) {
+  uint32_t w[4];
+  draw4(seed, 0u, sweep, PURPOSE_AXIS, 0u, w);
+  return (uint32_t)(((uint64_t)w[0] * (uint64_t)(2 * q)) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Initial configuration (paper: device_function_spinset; the distribution is
  * not stated, a uniformly random start is taken). */
 int oracle_init(int model, int dim, int L, int q, uint64_t seed, void* spins) {
@@ -169,6 +237,8 @@ int oracle_init(int model, int dim, int L, int q, uint64_t seed, void* spins) {
       ((int8_t*)spins)[i] = (w[0] >> 31) ? (int8_t)-1 : (int8_t)1;
     } else if (model == OR_POTTS) {
       ((uint8_t*)spins)[i] = (uint8_t)(((uint64_t)w[0] * (uint64_t)q) >> 32);
+    } else if (model == OR_CLOCK) {
+      ((uint16_t*)spins)[i] = (uint16_t)(((uint64_t)w[0] * (uint64_t)q) >> 32);
     } else {
       ((float*)spins)[i] = (float)(w[0] >> 8) * step;
     }
@@ -211,11 +281,18 @@ void oracle_bonds(int model, int dim, int L, int q, double T, uint64_t seed,
   float twoK = (float)(2.0 / T);
   uint32_t R[3][32];           /* bond sequences of the current row word */
   int64_t cached_g = -1;
+  const uint32_t* ctab = NULL;
+  uint32_t mirror = 0;
+  const int q2 = 2 * q;
+  if (model == OR_CLOCK) {
+    ctab = clock_table(q, T);
+    mirror = oracle_clock_mirror(seed, sweep, q);
+  }
   for (int64_t i = 0; i < N; ++i) {
     int64_t x = i % L;
     int64_t g = (i / L) * row_words(L) + (x >> 5);
     uint32_t w[4];
-    if (model == OR_XY) {
+    if (model == OR_XY || model == OR_CLOCK) {
       draw4(seed, (uint32_t)i, sweep, PURPOSE_BOND, 0u, w);
     } else if (g != cached_g) {
       for (int d = 0; d < dim; ++d) bond_sequence(seed, sweep, (uint32_t)g, d, R[d]);
@@ -230,6 +307,12 @@ void oracle_bonds(int model, int dim, int L, int q, double T, uint64_t seed,
       } else if (model == OR_POTTS) {
         active = (((const uint8_t*)spins)[i] == ((const uint8_t*)spins)[j]) &&
                  (bond_uniform(R[d], (int)(x & 31)) < t);
+      } else if (model == OR_CLOCK) {
+        const int pi_ = ((const uint16_t*)spins)[i];
+        const int pj_ = ((const uint16_t*)spins)[j];
+        const int ka = ((2 * pi_ - (int)mirror) % q2 + q2) % q2;
+        const int kb = ((2 * pj_ - (int)mirror) % q2 + q2) % q2;
+        active = w[d] < ctab[(size_t)ka * (size_t)q2 + (size_t)kb];
       } else {
         float ti = ((const float*)spins)[i];
         float tj = ((const float*)spins)[j];
@@ -290,6 +373,7 @@ int oracle_labels(int dim, int L, const uint32_t* planes, int32_t* labels) {
  *   XY:    reflect about the line perpendicular to r iff w >= 2^31:
  *          theta' = 2 phi + pi - theta, wrapped to [0, 2 pi)  (Wolff's
  *          embedded-cluster flip).
+ *   Clock: reflect iff w >= 2^31: p' = (s - p) mod q.
  * Returns the number of clusters (roots). */
 int64_t oracle_flip(int model, int dim, int L, int q, uint64_t seed, uint32_t sweep,
                     const int32_t* labels, void* spins) {
@@ -305,6 +389,7 @@ int64_t oracle_flip(int model, int dim, int L, int q, uint64_t seed, uint32_t sw
     ++nclusters;
   }
   double phi = (model == OR_XY) ? (double)oracle_xy_phi(seed, sweep) : 0.0;
+  const uint32_t clock_mirror = (model == OR_CLOCK) ? oracle_clock_mirror(seed, sweep, q) : 0u;
   const double two_pi = 6.283185307179586476925;
   const double pi = 3.141592653589793238463;
   for (int64_t i = 0; i < N; ++i) {
@@ -313,6 +398,11 @@ int64_t oracle_flip(int model, int dim, int L, int q, uint64_t seed, uint32_t sw
       ((int8_t*)spins)[i] = (w >> 31) ? (int8_t)-1 : (int8_t)1;
     } else if (model == OR_POTTS) {
       ((uint8_t*)spins)[i] = (uint8_t)(((uint64_t)w * (uint64_t)q) >> 32);
+    } else if (model == OR_CLOCK) {
+      if (w >> 31) {
+        const int p_ = ((uint16_t*)spins)[i];
+        ((uint16_t*)spins)[i] = (uint16_t)((((int)clock_mirror - p_) % q + q) % q);
+      }
     } else if (w >> 31) {
       double th = 2.0 * phi + pi - (double)((float*)spins)[i];
       while (th >= two_pi) th -= two_pi;
@@ -375,6 +465,29 @@ void oracle_moments(int model, int dim, int L, int q, const void* spins,
     rec->E = E;
     rec->M2 = (double)((int64_t)q * S2 - N * N) / (double)(q - 1);
     rec->Ed = (double)E;
+  } else if (model == OR_CLOCK) {
+    const uint16_t* s = (const uint16_t*)spins;
+    int64_t* n = (int64_t*)calloc((size_t)q, sizeof(int64_t));
+    int64_t* b = (int64_t*)calloc((size_t)q, sizeof(int64_t));
+    double* c = (double*)malloc(sizeof(double) * (size_t)q);
+    double* sn = (double*)malloc(sizeof(double) * (size_t)q);
+    oracle_clock_trig(q, c, sn);
+    for (int64_t i = 0; i < N; ++i) {
+      n[s[i]] += 1;
+      for (int d = 0; d < dim; ++d) b[((int)s[i] - (int)s[neighbour(dim, L, i, d)] + q) % q] += 1;
+    }
+    double mx = 0.0, my = 0.0, e = 0.0;
+    for (int k = 0; k < q; ++k) {
+      mx += (double)n[k] * c[k];
+      my += (double)n[k] * sn[k];
+      e -= (double)b[k] * c[k];
+    }
+    free(n); free(b); free(c); free(sn);
+    rec->mx = mx;
+    rec->my = my;
+    rec->e_xy = e;
+    rec->M2 = mx * mx + my * my;
+    rec->Ed = e;
   } else {
     const float* th = (const float*)spins;
     double mx = 0.0, my = 0.0, e = 0.0;
@@ -418,14 +531,17 @@ typedef struct {
   oracle_acc acc;
 } oracle_sw;
 
-static size_t spin_bytes(int model) { return model == OR_XY ? sizeof(float) : 1; }
+static size_t spin_bytes(int model) {
+  return model == OR_XY ? sizeof(float) : model == OR_CLOCK ? sizeof(uint16_t) : 1;
+}
 
 oracle_sw* oracle_create(int model, int dim, int L, int q, double T, uint64_t seed) {
-  if (model < 0 || model > 2 || dim < 2 || dim > 3 || L < 2 || !(T > 0.0)) return NULL;
+  if (model < 0 || model > 3 || dim < 2 || dim > 3 || L < 2 || !(T > 0.0)) return NULL;
   if (model == OR_POTTS && (q < 2 || q > 256)) return NULL;
+  if (model == OR_CLOCK && (q < 2 || q > 1024)) return NULL;
   oracle_sw* o = (oracle_sw*)calloc(1, sizeof(oracle_sw));
   if (!o) return NULL;
-  o->model = model; o->dim = dim; o->L = L; o->q = (model == OR_POTTS) ? q : 2;
+  o->model = model; o->dim = dim; o->L = L; o->q = (model == OR_POTTS || model == OR_CLOCK) ? q : 2;
   o->T = T; o->seed = seed; o->N = n_sites(dim, L); o->sweep = 0;
   o->spins = calloc((size_t)o->N, spin_bytes(model));
   o->planes = (uint32_t*)calloc((size_t)oracle_plane_words(dim, L), sizeof(uint32_t));

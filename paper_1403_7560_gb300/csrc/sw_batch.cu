@@ -172,7 +172,8 @@ void sw_batch_destroy(sw_batch* b) {
 
 int sw_batch_add(sw_batch* b, sw_handle* h) {
   if (!b || !h) return bfail(SW_ERR_BAD_ARG, "NULL argument");
-  if (h->model == SW_XY) return bfail(SW_ERR_BAD_ARG, "batches hold Ising and Potts lattices only");
+  if (h->model != SW_ISING && h->model != SW_POTTS)
+    return bfail(SW_ERR_BAD_ARG, "batches hold Ising and Potts lattices only");
   if (h->dim != b->dim) return bfail(SW_ERR_BAD_ARG, "lattice dimension differs from the batch's");
   if (h->batch) return bfail(SW_ERR_BAD_ARG, "lattice already belongs to a batch");
   b->members.push_back(h);
@@ -248,19 +249,19 @@ int sw_batch_sweep(sw_batch* b, int n) {
 }
 
 size_t sw_device_bytes(int model, int dim, int L, int q) {
-  if ((dim != 2 && dim != 3) || L < 4 || model < SW_ISING || model > SW_XY) return 0;
+  if ((dim != 2 && dim != 3) || L < 4 || model < SW_ISING || model > SW_CLOCK) return 0;
   double n = 1.0;
   for (int d = 0; d < dim; ++d) n *= L;
   if (n > 4294967295.0) return 0;
-  (void)q;
   int ntx, nty, ntz;
   swgb::tiles_for(dim, L, &ntx, &nty, &ntz);
   const size_t N = (size_t)n;
   const size_t words = (size_t)dim * (N / (size_t)L) * (size_t)((L + 31) / 32);
   const size_t ntiles = (size_t)ntx * nty * ntz;
-  const size_t spins = N * (model == SW_XY ? 4 : 1);
+  const size_t spins = N * (model == SW_XY ? 4 : model == SW_CLOCK ? 2 : 1);
+  const size_t clock = (model == SW_CLOCK) ? (size_t)4 * q * q * 4 + (size_t)2 * q * 16 : 0;
   return spins + 4 * words + 4 * N + ntiles * (size_t)swgb::merge_list_capacity(dim) * 4 + ntiles * 4 +
-         swgb::handle_block_bytes();
+         swgb::handle_block_bytes() + clock;
 }
 
 }  // extern "C"

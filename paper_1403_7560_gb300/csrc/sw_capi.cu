@@ -70,6 +70,34 @@ uint32_t bond_threshold(int model, double T) {
   return (uint32_t)t;
 }
 
+// Clock model tables, per the definition in include/sw.h: cos/sin of
+// (2 pi p)/q, and thresholds floor(-expm1(-(2/T) x_a x_b) 2^32) with
+// x_k = sin((pi k)/q), zero where x_a x_b <= 0.
+constexpr double kPi = 3.141592653589793238463;
+
+void clock_tables(int q, double T, std::vector<uint32_t>& tab, std::vector<double>& trig) {
+  const int q2 = 2 * q;
+  std::vector<double> x(q2);
+  for (int k = 0; k < q2; ++k) x[k] = std::sin((kPi * (double)k) / (double)q);
+  const double twoK = 2.0 / T;
+  tab.assign((size_t)q2 * q2, 0u);
+  for (int a = 0; a < q2; ++a)
+    for (int b = 0; b < q2; ++b) {
+      const double prod = x[a] * x[b];
+      if (prod > 0.0) {
+        double f = std::floor(-std::expm1(-(twoK * prod)) * 4294967296.0);
+        if (f > 4294967295.0) f = 4294967295.0;
+        tab[(size_t)a * q2 + b] = (uint32_t)f;
+      }
+    }
+  trig.assign(q2, 0.0);
+  for (int p = 0; p < q; ++p) {
+    const double ang = (2.0 * kPi * (double)p) / (double)q;
+    trig[p] = std::cos(ang);
+    trig[q + p] = std::sin(ang);
+  }
+}
+
 int draw_bits(int model, int q) {
   if (model != SW_POTTS) return 1;
   int b = 0;
@@ -86,6 +114,7 @@ void release(sw_handle* h) {
   cudaFree(h->lat.nhooked);
   cudaFree(h->d_labels);
   cudaFree(h->d_block);
+  cudaFree(h->d_clock);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -109,8 +138,9 @@ int check_device_error(sw_handle* h) {
 // sweep must write (0 if none).
 cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k, uint32_t* finalize) {
   *finalize = 0u;
-  if (h->model == SW_XY) {
-    cudaError_t e = swgb::launch_bonds_xy(h->lat, k, h->stream);
+  if (h->model == SW_XY || h->model == SW_CLOCK) {
+    cudaError_t e = (h->model == SW_XY) ? swgb::launch_bonds_xy(h->lat, k, h->stream)
+                                        : swgb::launch_bonds_clock(h->lat, k, h->stream);
     if (e != cudaSuccess) return e;
     return swgb::launch_label(h->lat, k, true, h->stream);
   }
@@ -150,7 +180,7 @@ cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas, measure, finalize, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->stream);
   if (e == cudaSuccess && measure) {
-    if (h->model == SW_XY) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+    if (h->model == SW_XY || h->model == SW_CLOCK) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
     else h->pending = k;
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], h->stream);
@@ -179,12 +209,13 @@ size_t sw_series_capacity(void) { return kSeriesCap; }
 
 sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) {
   g_last_error.clear();
-  if (model < SW_ISING || model > SW_XY) { fail(SW_ERR_BAD_ARG, "model must be 0 (Ising), 1 (Potts) or 2 (XY)"); return nullptr; }
+  if (model < SW_ISING || model > SW_CLOCK) { fail(SW_ERR_BAD_ARG, "model must be 0 (Ising), 1 (Potts), 2 (XY) or 3 (clock)"); return nullptr; }
   if (dim != 2 && dim != 3) { fail(SW_ERR_BAD_ARG, "dim must be 2 or 3"); return nullptr; }
   if (L < 4) { fail(SW_ERR_BAD_ARG, "L must be >= 4"); return nullptr; }
   if (!(T > 0.0) || !std::isfinite(T)) { fail(SW_ERR_BAD_ARG, "T must be finite and > 0"); return nullptr; }
   if (model == SW_POTTS && (q < 2 || q > 256)) { fail(SW_ERR_BAD_ARG, "Potts q must be in 2..256"); return nullptr; }
-  if (model != SW_POTTS) q = 2;
+  if (model == SW_CLOCK && (q < 2 || q > swgb::kMaxClockQ)) { fail(SW_ERR_BAD_ARG, "clock q must be in 2..1024"); return nullptr; }
+  if (model != SW_POTTS && model != SW_CLOCK) q = 2;
   const int sb = draw_bits(model, q);
   const double Nd = std::pow((double)L, dim);
   if (Nd * std::ldexp(1.0, sb + 1) > 4294967296.0) {
@@ -196,13 +227,14 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   sw_handle* h = new (std::nothrow) sw_handle();
   if (!h) { fail(SW_ERR_OOM, "host allocation"); return nullptr; }
   h->model = model; h->dim = dim; h->L = L; h->q = q; h->T = T; h->seed = seed;
-  h->spin_bytes = (size_t)N * (model == SW_XY ? sizeof(float) : 1);
+  h->spin_bytes = (size_t)N * (model == SW_XY ? sizeof(float) : model == SW_CLOCK ? sizeof(uint16_t) : 1);
 
   Lattice& lat = h->lat;
   lat.N = N; lat.L = L; lat.dim = dim; lat.W = (L + 31) / 32;
   lat.R = (uint32_t)(N / (uint32_t)L);
   swgb::tiles_for(dim, L, &lat.ntx, &lat.nty, &lat.ntz);
   lat.q = q; lat.sbits = sb;
+  lat.dq = (model == SW_POTTS) ? q : 2;
   lat.t_bond = (model == SW_XY) ? 0u : bond_threshold(model, T);
   lat.twoK = (float)(2.0 / T);
   lat.key0 = (uint32_t)(seed & 0xffffffffu);
@@ -244,6 +276,31 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   h->meas.xy_blocks = 0;
   h->meas.series = blk + off_series;
   h->meas.series_cap = kSeriesCap;
+
+  if (model == SW_CLOCK) {
+    // clock tables (thresholds, cos/sin) and histograms in one allocation
+    std::vector<uint32_t> tab;
+    std::vector<double> trig;
+    clock_tables(q, T, tab, trig);
+    const size_t tab_bytes = tab.size() * 4, trig_bytes = trig.size() * 8, hist_bytes = (size_t)2 * q * 8;
+    if ((e = cudaMalloc(&h->d_clock, tab_bytes + trig_bytes + hist_bytes)) != cudaSuccess) {
+      fail(SW_ERR_OOM, std::string("clock tables: ") + cudaGetErrorString(e));
+      cudaGetLastError();
+      release(h);
+      return nullptr;
+    }
+    char* c = static_cast<char*>(h->d_clock);
+    lat.ctab = reinterpret_cast<const uint32_t*>(c);
+    h->meas.ctrig = reinterpret_cast<const double*>(c + tab_bytes);
+    h->meas.chist = reinterpret_cast<unsigned long long*>(c + tab_bytes + trig_bytes);
+    if ((e = cudaMemcpy(c, tab.data(), tab_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c + tab_bytes, trig.data(), trig_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c + tab_bytes + trig_bytes, 0, hist_bytes)) != cudaSuccess) {
+      cuda_fail(e, "clock tables");
+      release(h);
+      return nullptr;
+    }
+  }
 
   if ((e = cudaMemsetAsync(h->d_block, 0, block_bytes, h->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(blk + off_series, 0xff, block_bytes - off_series, h->stream)) != cudaSuccess ||

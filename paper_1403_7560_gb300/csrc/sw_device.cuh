@@ -46,6 +46,13 @@ __device__ __forceinline__ float xy_phi(const Lattice& lat, uint32_t sweep) {
   return __fmul_rn((float)(w.x >> 8), 0x1.921fb6p-22f);
 }
 
+// Clock model mirror index of a sweep: s = floor(w 2q / 2^32), the
+// reflection p -> (s - p) mod q.
+__device__ __forceinline__ uint32_t clock_mirror(const Lattice& lat, uint32_t sweep) {
+  const uint4 w = philox(0u, sweep, kAxis, 0u, lat.key0, lat.key1);
+  return (uint32_t)(((unsigned long long)w.x * (unsigned)(2 * lat.q)) >> 32);
+}
+
 // One step of the bit-sliced comparison u < t, most significant bit first:
 // r holds bit `hb` of the 32 lanes' uniforms.
 __device__ __forceinline__ void cmp_step(uint32_t& lt, uint32_t& eq, uint32_t r, uint32_t t, int hb) {
@@ -262,6 +269,11 @@ __device__ __forceinline__ void add_histogram(const Lattice& lat, const Measure&
     if (s_hist[k]) atomicAdd(&slot[k], (unsigned long long)s_hist[k]);
 }
 
+template <int NW>
+__device__ __forceinline__ void commit_record(const Lattice& lat, const Measure& mb, uint32_t sweep,
+                                              long long M, long long E, long long S2, double mx,
+                                              double my, double exy, long long* s_ri);
+
 // Record of `sweep` and the FP64 accumulators, from the slot sums (Ising /
 // Potts) or the XY per-block partials, summed in a fixed order; the slots
 // and the sweep's cluster count are reset.  Called by all threads of ONE
@@ -310,6 +322,16 @@ __device__ __forceinline__ void finalize_record(const Lattice& lat, const Measur
     E = block_combine<NW>(warp_sum(c), s_ri);
     S2 = block_combine<NW>(warp_sum(g), s_ri);
   }
+  commit_record<NW>(lat, mb, sweep, M, E, S2, mx, my, exy, s_ri);
+}
+
+// Record of `sweep` from its gathered sums plus the sweep's cluster count
+// (slots reset), and the FP64 accumulators.  Called by all threads of one
+// block; thread 0 writes.
+template <int NW>
+__device__ __forceinline__ void commit_record(const Lattice& lat, const Measure& mb, uint32_t sweep,
+                                              long long M, long long E, long long S2, double mx,
+                                              double my, double exy, long long* s_ri) {
   long long nc = 0;
   unsigned long long* ncl_slots = mb.nclusters + kSlots * (sweep & 1u);
   for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {

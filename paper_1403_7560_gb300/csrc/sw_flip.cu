@@ -185,9 +185,13 @@ template <int MODEL>
 __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sweep, Measure mb,
                                                          bool count) {
   __shared__ float s_phi;
+  __shared__ uint32_t s_mirror;
   __shared__ long long s_red[kFlipWarps];
-  if (MODEL == kXY) {
-    if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
+  if (MODEL == kXY || MODEL == kClock) {
+    if (threadIdx.x == 0) {
+      if (MODEL == kXY) s_phi = xy_phi(lat, sweep);
+      else s_mirror = clock_mirror(lat, sweep);
+    }
     __syncthreads();
   }
   const int sb = lat.sbits, shift = sb + 1;
@@ -216,6 +220,12 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
         static_cast<int8_t*>(lat.spins)[i] = draw ? (int8_t)-1 : (int8_t)1;
       } else if (MODEL == kPotts) {
         static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)draw;
+      } else if (MODEL == kClock) {
+        if (draw) {
+          uint16_t* sp = static_cast<uint16_t*>(lat.spins);
+          const int q = lat.q;
+          sp[i] = (uint16_t)((((int)s_mirror - (int)sp[i]) % q + q) % q);
+        }
       } else if (draw) {
         float* th = static_cast<float*>(lat.spins);
         const float phi = s_phi;
@@ -319,6 +329,7 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
   k_compress<<<ntiles < kFlipBlocks ? ntiles : kFlipBlocks, kFlipThreads, 0, st>>>(lat, m, finalize);
   if (model == kIsing) k_apply<kIsing><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   else if (model == kPotts) k_apply<kPotts><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
+  else if (model == kClock) k_apply<kClock><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   else k_apply<kXY><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   return cudaGetLastError();
 }

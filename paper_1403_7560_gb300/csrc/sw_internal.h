@@ -13,7 +13,7 @@ struct sw_batch;
 
 namespace swgb {
 
-enum Model { kIsing = 0, kPotts = 1, kXY = 2 };
+enum Model { kIsing = 0, kPotts = 1, kXY = 2, kClock = 3 };
 
 // Device-side view of one lattice, passed by value to every kernel.
 struct Lattice {
@@ -30,6 +30,8 @@ struct Lattice {
   float twoK;           // XY: 2/T as float
   uint32_t key0, key1;  // Philox key = seed
   int model;            // Model
+  int dq;               // modulus of the cluster draw: q (Potts) or 2
+  const uint32_t* ctab; // clock: bond thresholds [2q][2q]
   uint32_t* hooked;     // per tile: roots hooked by the merge [ntiles * hook_cap]
   uint32_t* nhooked;    // per tile: number of hooked roots [ntiles]
   int hook_cap;         // capacity of a tile's hooked list
@@ -45,6 +47,8 @@ struct Measure {
   unsigned long long* sums;       // [kSlots][2]: integer M, E (two's complement)
   unsigned long long* hist;       // [kSlots][256]: Potts histogram
   double* part_d;                 // XY per-block partials [3 * kMeasureBlocks]
+  unsigned long long* chist;      // clock: histograms of states [q] and bond differences [q]
+  const double* ctrig;            // clock: cos(2 pi p / q) [q], sin [q]
   int xy_blocks;                  // blocks that wrote part_d
   double* acc;                    // n, sum M2, M4, E, E2, nclusters
   void* series;                   // sw_record ring
@@ -77,7 +81,8 @@ struct Record {
   double mx, my, e_xy, M2, Ed;
 };
 
-constexpr int kMeasureBlocks = 1216;  // 152 SMs x 8 blocks of 256 threads
+constexpr int kMeasureBlocks = 1216;
+constexpr int kMaxClockQ = 1024;  // largest q of the clock model  // 152 SMs x 8 blocks of 256 threads
 
 // Tile shape of the labeling, merge and flip kernels: 32 sites along x (one
 // bit-plane word) by TY (by TZ); one CTA of TY*TZ threads per tile.
@@ -97,6 +102,8 @@ void set_last_error(const std::string& msg);
 cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
 // Bonds of the XY model (lane per site) into the bit-planes.
 cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, cudaStream_t st);
+// Bonds of the clock model (lane per site, table thresholds).
+cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, cudaStream_t st);
 // Tile labels (+ Ising/Potts bonds when from_mask is false; cluster draws
 // when sweep != 0) into the forest.
 cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st);
@@ -144,5 +151,6 @@ struct sw_handle {
   uint64_t pending = 0;         // measured sweep whose record is not yet written
   int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
   void* d_block = nullptr;      // one allocation holding every small buffer
+  void* d_clock = nullptr;      // clock model: thresholds, cos/sin, histograms
   struct sw_batch* batch = nullptr;  // batch the lattice belongs to, if any
 };

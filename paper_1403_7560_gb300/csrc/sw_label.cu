@@ -206,7 +206,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
               cached = i >> 2;
               w = philox(cached, sweep, kDraw, 0u, lat.key0, lat.key1);
             }
-            packed |= draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.q) << (8 * t);
+            packed |= draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.dq) << (8 * t);
           }
         }
         sdraw[j * (ROWS + 1) + r] = packed;
@@ -353,7 +353,60 @@ __global__ void __launch_bounds__(256) k_bonds_xy(Lattice lat, uint32_t sweep) {
   }
 }
 
+// ---------------------------------------------------------------- clock bonds
+// q-state clock: x_i = sin(pi k_i / q), k_i = (2 p_i - s) mod 2q for the
+// sweep's mirror index s; bond (i,d) active iff u(i,d) < t[k_i][k_j] (the
+// table is 0 where x_i x_j <= 0); u(i,d) = word d of Philox(i, sweep, BOND, 0).
+template <int D>
+__global__ void __launch_bounds__(256) k_bonds_clock(Lattice lat, uint32_t sweep) {
+  __shared__ uint32_t s_mirror;
+  if (threadIdx.x == 0) s_mirror = clock_mirror(lat, sweep);
+  __syncthreads();
+  const int L = lat.L, lane = threadIdx.x & 31;
+  const int q2 = 2 * lat.q;
+  const int mirror = (int)s_mirror;
+  const uint32_t nwords = lat.R * (uint32_t)lat.W;
+  const uint32_t plane = nwords;
+  const uint16_t* sp = static_cast<const uint16_t*>(lat.spins);
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t g = gw; g < nwords; g += nw) {
+    const uint32_t row = g / (uint32_t)lat.W, xw = g % (uint32_t)lat.W;
+    const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
+    const int x = (int)(32 * xw) + lane;
+    uint32_t a = 0u;
+    if (x < L) {
+      const uint32_t i = (uint32_t)x + (uint32_t)L * row;
+      const uint4 w = philox(i, sweep, kBond, 0u, lat.key0, lat.key1);
+      uint32_t jn[3];
+      jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
+      jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
+      jn[2] = (D == 3) ? ((z + 1 == (uint32_t)L) ? i - z * L * L : i + (uint32_t)L * L) : 0u;
+      const int ki = ((2 * (int)sp[i] - mirror) % q2 + q2) % q2;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const int kj = ((2 * (int)sp[jn[d]] - mirror) % q2 + q2) % q2;
+        a |= (uint32_t)(word_of(w, d) < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj])) << d;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const uint32_t bal = __ballot_sync(kFull, (a >> d) & 1u);
+      if (lane == d) lat.planes[d * plane + g] = bal;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, cudaStream_t st) {
+  const uint32_t words = lat.R * (uint32_t)lat.W;
+  unsigned g = (words + 7u) / 8u;
+  if (g > 4096u) g = 4096u;
+  if (lat.dim == 2) k_bonds_clock<2><<<g, 256, 0, st>>>(lat, sweep);
+  else k_bonds_clock<3><<<g, 256, 0, st>>>(lat, sweep);
+  return cudaGetLastError();
+}
 
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz) {
   *ntx = (L + 31) / 32;

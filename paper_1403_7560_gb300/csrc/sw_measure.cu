@@ -23,6 +23,8 @@ __global__ void __launch_bounds__(256) k_init(Lattice lat) {
       static_cast<int8_t*>(lat.spins)[i] = (w >> 31) ? (int8_t)-1 : (int8_t)1;
     } else if (MODEL == kPotts) {
       static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)draw_value(w, (uint32_t)lat.q);
+    } else if (MODEL == kClock) {
+      static_cast<uint16_t*>(lat.spins)[i] = (uint16_t)draw_value(w, (uint32_t)lat.q);
     } else {
       static_cast<float*>(lat.spins)[i] = __fmul_rn((float)(w >> 8), 0x1.921fb6p-22f);
     }
@@ -33,12 +35,12 @@ constexpr int kMThreads = 256, kMWarps = kMThreads / 32;
 
 template <int MODEL, int D>
 __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t sweep, Measure mb) {
-  __shared__ unsigned int s_hist[256];
+  __shared__ unsigned int s_hist[MODEL == kClock ? 2 * kMaxClockQ : 256];
   __shared__ long long s_ri[kMWarps];
   __shared__ double s_rd[kMWarps];
   const int L = lat.L, lane = threadIdx.x & 31;
-  if (MODEL == kPotts) {
-    for (int k = threadIdx.x; k < lat.q; k += blockDim.x) s_hist[k] = 0u;
+  if (MODEL == kPotts || MODEL == kClock) {
+    for (int k = threadIdx.x; k < (MODEL == kClock ? 2 * lat.q : lat.q); k += blockDim.x) s_hist[k] = 0u;
     __syncthreads();
   }
   long long m = 0, e = 0;
@@ -73,6 +75,14 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
         for (int d = 0; d < D; ++d) e += (s[jn[d]] != si) ? 1 : 0;
         const unsigned grp = __match_any_sync(__activemask(), si);
         if (lane == __ffs(grp) - 1) atomicAdd(&s_hist[si], (unsigned)__popc(grp));
+      } else if (MODEL == kClock) {
+        // histograms of states and of bond differences (p_i - p_j) mod q
+        const uint16_t* sp = static_cast<const uint16_t*>(lat.spins);
+        const int q = lat.q;
+        const int pi = sp[i];
+        atomicAdd(&s_hist[pi], 1u);
+#pragma unroll
+        for (int d = 0; d < D; ++d) atomicAdd(&s_hist[q + (pi - (int)sp[jn[d]] + q) % q], 1u);
       } else {
         const float* th = static_cast<const float*>(lat.spins);
         const float ti = th[i];
@@ -88,6 +98,12 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
   if (MODEL == kPotts) {
     __syncthreads();
     add_histogram(lat, mb, blockIdx.x, s_hist);
+  }
+  if (MODEL == kClock) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * lat.q; k += blockDim.x)
+      if (s_hist[k]) atomicAdd(&mb.chist[k], (unsigned long long)s_hist[k]);
+    return;
   }
   if (MODEL != kXY) {
     add_integer_sums<kMWarps>(mb, blockIdx.x, m, e, s_ri);
@@ -108,7 +124,34 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
 __global__ void __launch_bounds__(kMThreads) k_finalize(Lattice lat, uint32_t sweep, Measure mb) {
   __shared__ long long s_ri[kMWarps];
   __shared__ double s_rd[kMWarps];
-  finalize_record<kMWarps>(lat, mb, sweep, s_ri, s_rd);
+  __shared__ unsigned long long s_h[2 * kMaxClockQ];
+  __shared__ double s_m[3];
+  if (lat.model != kClock) {
+    finalize_record<kMWarps>(lat, mb, sweep, s_ri, s_rd);
+    return;
+  }
+  // clock: Mx = sum_p n_p cos_p, My = sum_p n_p sin_p, E = -sum_D b_D cos_D,
+  // in index order from the integer histograms
+  const int q = lat.q;
+  for (int k = threadIdx.x; k < 2 * q; k += blockDim.x) {
+    s_h[k] = __ldcg(&mb.chist[k]);
+    mb.chist[k] = 0ull;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0, my = 0.0, e = 0.0;
+    for (int k = 0; k < q; ++k) {
+      const double c = mb.ctrig[k], sn = mb.ctrig[q + k];
+      mx = __dadd_rn(mx, __dmul_rn((double)s_h[k], c));
+      my = __dadd_rn(my, __dmul_rn((double)s_h[k], sn));
+      e = __dsub_rn(e, __dmul_rn((double)s_h[q + k], c));
+    }
+    s_m[0] = mx;
+    s_m[1] = my;
+    s_m[2] = e;
+  }
+  __syncthreads();
+  commit_record<kMWarps>(lat, mb, sweep, 0, 0, 0, s_m[0], s_m[1], s_m[2], s_ri);
 }
 
 unsigned grid_for(uint32_t n_warps_work, unsigned cap) {
@@ -123,6 +166,7 @@ cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st) {
   if (g > 4096u) g = 4096u;
   if (model == kIsing) k_init<kIsing><<<g, 256, 0, st>>>(lat);
   else if (model == kPotts) k_init<kPotts><<<g, 256, 0, st>>>(lat);
+  else if (model == kClock) k_init<kClock><<<g, 256, 0, st>>>(lat);
   else k_init<kXY><<<g, 256, 0, st>>>(lat);
   return cudaGetLastError();
 }
@@ -133,10 +177,12 @@ cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const 
   if (lat.dim == 2) {
     if (model == kIsing) k_measure<kIsing, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else if (model == kPotts) k_measure<kPotts, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
+    else if (model == kClock) k_measure<kClock, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else k_measure<kXY, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
   } else {
     if (model == kIsing) k_measure<kIsing, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else if (model == kPotts) k_measure<kPotts, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
+    else if (model == kClock) k_measure<kClock, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else k_measure<kXY, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
   }
   Measure mf = m;

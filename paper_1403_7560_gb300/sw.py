@@ -13,7 +13,7 @@ import numpy as np
 
 from . import build as _build
 
-SW_ISING, SW_POTTS, SW_XY = 0, 1, 2
+SW_ISING, SW_POTTS, SW_XY, SW_CLOCK = 0, 1, 2, 3
 SW_OK, SW_ERR_BAD_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_RANGE = 0, -1, -2, -3, -4, -5
 
 _lock = threading.Lock()
@@ -110,7 +110,7 @@ def _check(rc: int):
 
 
 def spin_dtype(model: int):
-    return {SW_ISING: np.int8, SW_POTTS: np.uint8, SW_XY: np.float32}[model]
+    return {SW_ISING: np.int8, SW_POTTS: np.uint8, SW_XY: np.float32, SW_CLOCK: np.uint16}[model]
 
 
 class Handle:

@@ -151,3 +151,16 @@ def xy_metropolis(dim: int, L: int, T: float, chains: int, sweeps: int, burn: in
     e, m = eacc / nmeas, macc / nmeas
     return {"E": e.mean(), "E_err": e.std(ddof=1) / math.sqrt(chains),
             "M2": m.mean(), "M2_err": m.std(ddof=1) / math.sqrt(chains)}
+
+
+def enumerate_clock(dim: int, L: int, q: int, T: float) -> dict:
+    """Exact <E>, <M^2>, <M^4> of the q-state clock model
+    H = -sum cos(theta_i - theta_j), theta = 2 pi p / q, by enumeration."""
+    N = L ** dim
+    states = (np.arange(q ** N)[:, None] // (q ** np.arange(N))) % q
+    th = 2 * np.pi * states / q
+    E = -sum(np.cos(th - th[:, neighbours(dim, L, d)]).sum(-1) for d in range(dim))
+    M2 = np.cos(th).sum(-1) ** 2 + np.sin(th).sum(-1) ** 2
+    w = np.exp(-(E - E.min()) / T)
+    Z = w.sum()
+    return {"E": (w * E).sum() / Z, "M2": (w * M2).sum() / Z, "M4": (w * M2 ** 2).sum() / Z}

@@ -10,7 +10,7 @@ import math
 
 import numpy as np
 
-ISING, POTTS, XY = 0, 1, 2
+ISING, POTTS, XY, CLOCK = 0, 1, 2, 3
 
 # Critical couplings quoted for the workloads.
 TC_2D_ISING = 2.0 / math.log(1.0 + math.sqrt(2.0))      # 2.269185...
@@ -31,7 +31,7 @@ WORKLOADS = {
 
 
 def spin_dtype(model: int):
-    return {ISING: np.int8, POTTS: np.uint8, XY: np.float32}[model]
+    return {ISING: np.int8, POTTS: np.uint8, XY: np.float32, CLOCK: np.uint16}[model]
 
 
 def random_spins(model: int, n: int, q: int, seed: int) -> np.ndarray:
@@ -40,6 +40,8 @@ def random_spins(model: int, n: int, q: int, seed: int) -> np.ndarray:
         return (rng.integers(0, 2, n, dtype=np.int8) * 2 - 1).astype(np.int8)
     if model == POTTS:
         return rng.integers(0, q, n).astype(np.uint8)
+    if model == CLOCK:
+        return rng.integers(0, q, n).astype(np.uint16)
     return (rng.random(n, dtype=np.float32) * np.float32(2 * np.pi)).astype(np.float32) % np.float32(2 * np.pi)
 
 

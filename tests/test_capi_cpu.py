@@ -39,7 +39,9 @@ def test_library_exports_every_declared_symbol(swlib):
 
 
 @pytest.mark.parametrize("args,needle", [
-    ((3, 2, 16, 2, 2.0, 1), "model"),
+    ((4, 2, 16, 2, 2.0, 1), "model"),
+    ((3, 2, 16, 1, 1.0, 1), "clock q"),
+    ((3, 2, 16, 1025, 1.0, 1), "clock q"),
     ((0, 4, 16, 2, 2.0, 1), "dim"),
     ((0, 2, 3, 2, 2.0, 1), "L must"),
     ((0, 2, 16, 2, 0.0, 1), "T must"),

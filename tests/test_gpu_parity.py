@@ -15,7 +15,7 @@ import pytest
 
 import inputs
 import oracle
-from oracle import ISING, POTTS, XY
+from oracle import CLOCK, ISING, POTTS, XY
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +33,8 @@ def sw():
 
 
 def record_key(model):
+    if model == CLOCK:
+        return ("mx", "my", "e_xy", "nclusters")
     return ("M", "E", "nclusters") if model == ISING else ("E", "S2", "nclusters")
 
 
@@ -62,7 +64,8 @@ def run_exact_parity(sw, model, dim, L, q, T, seed, sweeps, check_labels=True):
 
 @pytest.mark.parametrize("model,dim,L,q", [
     (ISING, 2, 4, 2), (ISING, 2, 48, 2), (ISING, 3, 5, 2), (ISING, 3, 40, 2),
-    (POTTS, 2, 33, 3), (POTTS, 3, 17, 4), (POTTS, 2, 16, 256), (XY, 2, 20, 2), (XY, 3, 9, 2)])
+    (POTTS, 2, 33, 3), (POTTS, 3, 17, 4), (POTTS, 2, 16, 256), (XY, 2, 20, 2), (XY, 3, 9, 2),
+    (CLOCK, 2, 20, 512), (CLOCK, 3, 9, 7)])
 def test_initial_state(sw, model, dim, L, q):
     h = sw.sw_create(model, dim, L, q, 1.0, 77)
     try:
@@ -84,6 +87,20 @@ def test_ising_sweeps_bit_exact(sw, dim, L, T):
     (3, 16, 3, 1.8), (3, 24, 8, 1.3)])
 def test_potts_sweeps_bit_exact(sw, dim, L, q, T):
     run_exact_parity(sw, POTTS, dim, L, q, T, seed=2000 + L, sweeps=12)
+
+
+@pytest.mark.parametrize("dim,L,q,T", [
+    (2, 32, 512, 0.9), (2, 48, 8, 1.0), (2, 37, 3, 0.7), (3, 16, 512, 2.2), (3, 20, 6, 2.0),
+    (3, 9, 1024, 2.1)])
+def test_clock_sweeps_bit_exact(sw, dim, L, q, T):
+    """The q-state clock model (the paper's discretised XY): trajectories and
+    float moments are reproducible bit for bit."""
+    run_exact_parity(sw, CLOCK, dim, L, q, T, seed=4000 + L, sweeps=10)
+
+
+def test_clock_config_3d_L64_q512(sw):
+    """3D clock q=512 (Sec. 3's XY runs) near its critical temperature."""
+    run_exact_parity(sw, CLOCK, 3, 64, 512, 2.20184, seed=1002, sweeps=3)
 
 
 @pytest.mark.parametrize("model,dim,L,q,T", [

@@ -320,3 +320,71 @@ def test_resume_from_state_is_exact():
     a.sweep(5)
     b.sweep(5)
     assert np.array_equal(a.spins, b.spins)
+
+
+# ----------------------------------------------------------------- clock model
+CLOCK = oracle.CLOCK
+
+
+def test_clock_q4_is_two_ising_models_at_twice_the_temperature():
+    # cos(t_i - t_j) = (s_i s_j + u_i u_j)/2 with s = cos + sin, u = cos - sin
+    # in {+1,-1}: the 4-state clock at T is two independent Ising models at 2T.
+    T = 1.2
+    ex = exact.enumerate_ising(2, 4, 2 * T)
+    o = oracle.Oracle(CLOCK, 2, 4, 4, T, seed=12)
+    o.sweep(300, measure=False)
+    mean, err = _binned(o, 24, 6000)
+    # E = (E_s + E_u)/2 and M^2 = (M_s^2 + M_u^2)/2 of the two Ising models
+    assert abs(mean[0] - ex["E"]) < 4.5 * err[0] and abs(mean[1] - ex["M2"]) < 4.5 * err[1]
+    # the larger lattice against Kaufman's exact energy at 2T (critical point)
+    o = oracle.Oracle(CLOCK, 2, 16, 4, 2.269185 / 2, seed=13)
+    o.sweep(200, measure=False)
+    mean, err = _binned(o, 20, 1500)
+    kf = exact.kaufman_energy(16, 2.269185)
+    assert abs(mean[0] - kf) < 4.5 * err[0], (mean[0], kf, err[0])
+
+
+@pytest.mark.parametrize("dim,L,q,T", [(2, 3, 3, 0.8), (2, 3, 5, 0.9), (3, 2, 6, 1.5)])
+def test_clock_stationary_law_enumeration(dim, L, q, T):
+    ex = exact.enumerate_clock(dim, L, q, T)
+    o = oracle.Oracle(CLOCK, dim, L, q, T, seed=71 + q)
+    o.sweep(300, measure=False)
+    mean, err = _binned(o, 24, 5000)
+    _check(mean, err, ex, ["E", "M2", "M4", None])
+
+
+def test_clock_512_approaches_xy():
+    dim, L, T = 2, 4, 1.0
+    ref = exact.xy_metropolis(dim, L, T, chains=400, sweeps=1500, burn=200, seed=23)
+    o = oracle.Oracle(CLOCK, dim, L, 512, T, seed=29)
+    o.sweep(300, measure=False)
+    mean, err = _binned(o, 20, 5000)
+    for j, key in [(0, "E"), (1, "M2")]:
+        sig = math.hypot(err[j], ref[key + "_err"])
+        assert abs(mean[j] - ref[key]) < 4.5 * sig, (key, mean[j], ref[key], sig)
+
+
+def test_clock_bonds_and_reflection():
+    dim, L, q, T, seed = 2, 48, 64, 0.8, 3
+    s = inputs.random_spins(CLOCK, L * L, q, seed=4)
+    n_on, p_sum, var = 0, 0.0, 0.0
+    for k in range(1, 21):
+        m = oracle.clock_mirror(seed, k, q)
+        assert 0 <= m < 2 * q
+        x = np.sin(np.pi * ((2 * s.astype(np.int64) - m) % (2 * q)) / q)
+        bits = inputs.unpack_planes(oracle.bonds(CLOCK, dim, L, q, T, seed, k, s), dim, L)
+        for d in range(dim):
+            prod = x * x[exact.neighbours(dim, L, d)]
+            assert not (bits[d] & (prod <= 0)).any()
+            p = np.where(prod > 0, -np.expm1(-2.0 / T * prod), 0.0)
+            n_on += bits[d].sum()
+            p_sum += p.sum()
+            var += (p * (1 - p)).sum()
+        lab = oracle.labels(dim, L, oracle.bonds(CLOCK, dim, L, q, T, seed, k, s))
+        new, _ = oracle.flip(CLOCK, dim, L, q, seed, k, lab, s)
+        moved = new != s                          # sites on the mirror line stay put
+        xn = np.sin(np.pi * ((2 * new.astype(np.int64) - m) % (2 * q)) / q)
+        assert np.allclose(xn[moved], -x[moved], atol=1e-12)
+        assert np.all((new[moved].astype(np.int64) + s[moved]) % q == m % q)
+        s = new
+    assert abs(n_on - p_sum) < 5 * math.sqrt(var)
