@@ -265,6 +265,23 @@ def run_gpu(args):
         upd.append(a.elapsed_time(b))
     update_only = N_SITES / (statistics.mean(upd) * 1e6)
 
+    # the paper's labeler (label equivalence) against the tile union-find on
+    # the bond planes of the same sweeps, each producing canonical labels
+    lab_uf, lab_le, lab_it = [], [], []
+    for k in range(5):
+        sw.sw_sweep(h, 1)
+        flush.fill_(1)
+        lab_uf.append(sw.sw_relabel(h, sw.SW_LABEL_TILE_UF, False)[1])
+        flush.fill_(2)
+        _, ms, it = sw.sw_relabel(h, sw.SW_LABEL_EQUIVALENCE, False)
+        lab_le.append(ms)
+        lab_it.append(it)
+    labeling = {"planes": "bonds of 5 measured sweeps after the timed ones",
+                "tile_uf_ms": statistics.mean(lab_uf),
+                "label_equivalence_ms": statistics.mean(lab_le),
+                "label_equivalence_iterations": statistics.mean(lab_it),
+                "speedup": statistics.mean(lab_le) / statistics.mean(lab_uf)}
+
     # end to end through the C ABI with pinned host buffers
     host_in = torch.empty(N_SITES, dtype=torch.int8, pin_memory=True).numpy()
     host_out = torch.empty(N_SITES, dtype=torch.int8, pin_memory=True).numpy()
@@ -299,6 +316,7 @@ def run_gpu(args):
                          "bytes_per_site": bps},
             "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
             "update_only": {"value": update_only, "unit": UNIT},
+            "labeling": labeling,
             "b_ref": {"bytes_per_site": B_REF, "GBps": value * B_REF, "frac": value * B_REF / peak},
             "gpu_launches": KERNELS_PER_SWEEP * args.steps,
             "clocks": clk,

@@ -190,6 +190,31 @@ int sw_get_bonds(sw_handle* h, uint32_t* host, size_t words);
  * spins are untouched).  For parity tests of the labeling step. */
 int sw_label_from_bonds(sw_handle* h, const uint32_t* host_mask, int32_t* host_labels);
 
+/* Label the handle's current bond planes (those of the last sweep, or of
+ * the last sw_label_from_bonds) with one of two methods and time it:
+ *   SW_LABEL_TILE_UF      the sweep's own labeling: union-find inside
+ *                         32-wide tiles in shared memory, then a merge of
+ *                         the tile-local roots across tile faces;
+ *   SW_LABEL_EQUIVALENCE  the labeler the paper runs (Sec. 2, label
+ *                         equivalence of Hawick et al. in the refinement of
+ *                         Kalentev et al.): a scanning kernel lowers the
+ *                         entry of each site's root to the smallest bonded
+ *                         label, an analysis kernel jumps every label to its
+ *                         root, and the host reads a change flag after each
+ *                         iteration until a scan changes nothing.
+ * Both write the same canonical labels (min site index per cluster) to the
+ * handle's label buffer; host_labels (N int32, may be NULL) receives a copy.
+ * *ms (may be NULL) gets the device time between events recorded on the
+ * handle's stream around the labeling only (for EQUIVALENCE it includes the
+ * per-iteration flag reads); *iterations (may be NULL) the number of
+ * scan + analysis passes (1 for TILE_UF).  Synchronous.  The spins, the
+ * sweep counter and the measurement state are untouched; the tile forest is
+ * rebuilt by TILE_UF and left alone by EQUIVALENCE.  Errors: SW_ERR_BAD_ARG
+ * (NULL handle, unknown method), SW_ERR_CUDA (launch or allocation failure;
+ * message in sw_last_error). */
+enum sw_label_method { SW_LABEL_TILE_UF = 0, SW_LABEL_EQUIVALENCE = 1 };
+int sw_relabel(sw_handle* h, int method, int32_t* host_labels, float* ms, int* iterations);
+
 /* One measured sweep, like sw_sweep(h, 1), with CUDA events recorded on
  * the handle's stream between its kernels.  Synchronises, then writes the
  * device time of each phase in milliseconds to phase_ms[0..3]:

@@ -62,6 +62,7 @@ _SIGNATURES = {
     "sw_get_labels": (_i, [_vp, _vp, _sz]),
     "sw_get_bonds": (_i, [_vp, _vp, _sz]),
     "sw_label_from_bonds": (_i, [_vp, _vp, _vp]),
+    "sw_relabel": (_i, [_vp, _i, _vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i)]),
     "sw_get_series": (_i, [_vp, _u64, _sz, ctypes.POINTER(sw_record)]),
     "sw_series_capacity": (_sz, []),
     "sw_sweep_timed": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
@@ -77,6 +78,7 @@ _SIGNATURES = {
 }
 
 SW_NOALLOC_MAX_SITES = 1 << 21
+SW_LABEL_TILE_UF, SW_LABEL_EQUIVALENCE = 0, 1
 
 
 def library_path() -> str:
@@ -219,6 +221,17 @@ def sw_label_from_bonds(h: Handle, mask: np.ndarray) -> np.ndarray:
     out = np.empty(h.N, dtype=np.int32)
     _check(lib().sw_label_from_bonds(h, m.ctypes.data, out.ctypes.data))
     return out
+
+
+def sw_relabel(h: Handle, method: int, want_labels: bool = True):
+    """Label the handle's current bond planes with SW_LABEL_TILE_UF or
+    SW_LABEL_EQUIVALENCE; returns (labels or None, device ms, iterations)."""
+    out = np.empty(h.N, dtype=np.int32) if want_labels else None
+    ms = ctypes.c_float(0.0)
+    it = ctypes.c_int(0)
+    _check(lib().sw_relabel(h, method, out.ctypes.data if want_labels else None,
+                            ctypes.byref(ms), ctypes.byref(it)))
+    return out, float(ms.value), int(it.value)
 
 
 def sw_get_series(h: Handle, first: int, count: int) -> list[dict]:
