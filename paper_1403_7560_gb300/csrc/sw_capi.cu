@@ -237,8 +237,7 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   lat.dq = (model == SW_POTTS) ? q : 2;
   lat.t_bond = (model == SW_XY) ? 0u : bond_threshold(model, T);
   lat.twoK = (float)(2.0 / T);
-  lat.key0 = (uint32_t)(seed & 0xffffffffu);
-  lat.key1 = (uint32_t)(seed >> 32);
+  swgb::set_philox_key(lat, seed);
   lat.model = model;
   h->bond_words = (size_t)dim * lat.R * (size_t)lat.W;
   const size_t ntiles = (size_t)lat.ntx * lat.nty * lat.ntz;

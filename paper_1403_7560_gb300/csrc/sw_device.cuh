@@ -17,21 +17,20 @@ constexpr uint32_t kInit = 0u, kBond = 1u, kDraw = 2u, kAxis = 3u;
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds; per round two 32x32
 // multiplications whose high words are xor-ed with the other counter words
-// and the round key, key bumped by the Weyl increments between rounds.
+// and the round key.  The round keys (the key bumped by the Weyl increments
+// r times) are precomputed per lattice and read from the kernel parameters.
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        uint32_t k0, uint32_t k1) {
+                                        const uint32_t* rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
     const uint32_t lo0 = 0xD2511F53u * c0;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
     const uint32_t lo1 = 0xCD9E8D57u * c2;
-    c0 = hi1 ^ c1 ^ k0;
+    c0 = hi1 ^ c1 ^ rk[2 * r];
     c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
+    c2 = hi0 ^ c3 ^ rk[2 * r + 1];
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
 }
@@ -42,14 +41,14 @@ __device__ __forceinline__ uint32_t word_of(const uint4& w, int j) {
 
 // XY mirror direction of a sweep: phi = (w0 >> 8) * fl(2 pi)/2^24 in float.
 __device__ __forceinline__ float xy_phi(const Lattice& lat, uint32_t sweep) {
-  const uint4 w = philox(0u, sweep, kAxis, 0u, lat.key0, lat.key1);
+  const uint4 w = philox(0u, sweep, kAxis, 0u, lat.rk);
   return __fmul_rn((float)(w.x >> 8), 0x1.921fb6p-22f);
 }
 
 // Clock model mirror index of a sweep: s = floor(w 2q / 2^32), the
 // reflection p -> (s - p) mod q.
 __device__ __forceinline__ uint32_t clock_mirror(const Lattice& lat, uint32_t sweep) {
-  const uint4 w = philox(0u, sweep, kAxis, 0u, lat.key0, lat.key1);
+  const uint4 w = philox(0u, sweep, kAxis, 0u, lat.rk);
   return (uint32_t)(((unsigned long long)w.x * (unsigned)(2 * lat.q)) >> 32);
 }
 
@@ -67,14 +66,15 @@ __device__ __forceinline__ void cmp_step(uint32_t& lt, uint32_t& eq, uint32_t r,
 // Bernoulli word of row word g, direction d: bit b is set iff the 32-bit
 // uniform u(b) < t, where bit 31-k of u(b) is bit b of the k-th word of the
 // sequence, word k = word (k & 3) of Philox(g, sweep, BOND, 8d + k/4).  The
-// comparison stops once every lane is decided; undecided lanes after 32
-// bits have u == t and stay 0.
+// comparison covers only the lanes in `live` (the others are masked off by
+// the caller) and stops once all of them are decided; undecided lanes
+// after 32 bits have u == t and stay 0.
 __device__ __forceinline__ uint32_t bernoulli_word(uint32_t g, uint32_t sweep, int d, uint32_t t,
-                                                   uint32_t k0, uint32_t k1) {
-  uint32_t lt = 0u, eq = kFull;
+                                                   uint32_t live, const uint32_t* rk) {
+  uint32_t lt = 0u, eq = live;
 #pragma unroll 1
   for (int c = 0; c < 8; ++c) {
-    const uint4 w = philox(g, sweep, kBond, (uint32_t)(8 * d + c), k0, k1);
+    const uint4 w = philox(g, sweep, kBond, (uint32_t)(8 * d + c), rk);
     const int hb = 31 - 4 * c;
     cmp_step(lt, eq, w.x, t, hb);
     cmp_step(lt, eq, w.y, t, hb - 1);

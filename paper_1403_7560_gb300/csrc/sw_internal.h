@@ -29,6 +29,7 @@ struct Lattice {
   uint32_t t_bond;      // Ising/Potts: bond active iff draw < t_bond
   float twoK;           // XY: 2/T as float
   uint32_t key0, key1;  // Philox key = seed
+  uint32_t rk[20];      // Philox round keys: (key0 + r*0x9E3779B9, key1 + r*0xBB67AE85), r = 0..9
   int model;            // Model
   int dq;               // modulus of the cluster draw: q (Potts) or 2
   const uint32_t* ctab; // clock: bond thresholds [2q][2q]
@@ -36,6 +37,16 @@ struct Lattice {
   uint32_t* nhooked;    // per tile: number of hooked roots [ntiles]
   int hook_cap;         // capacity of a tile's hooked list
 };
+
+// Sets the Philox key (seed low, seed high) and its ten round keys.
+inline void set_philox_key(Lattice& lat, uint64_t seed) {
+  lat.key0 = (uint32_t)(seed & 0xffffffffu);
+  lat.key1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    lat.rk[2 * r] = lat.key0 + (uint32_t)r * 0x9E3779B9u;
+    lat.rk[2 * r + 1] = lat.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
 
 // Buffers of the moment reduction (the per-sweep record and accumulators).
 // Integer sums are spread over kSlots slots (by block index) so that no

@@ -7,12 +7,14 @@
 //     byte-lane compares, AND a bit-sliced Bernoulli word per direction
 //     (u < t decided for 32 sites at once from whole Philox words) -- and
 //     the row's cluster draws; or the bonds read from the bit-planes.
-//   phase 2 (lane per site): every site's parent is the start of its x-run.
-//   phase 3 (thread per row word): one shared-memory union per pair of runs
+//   Before it, every site is its own parent in the shared-memory forest; an
+//   x-run is represented by its start, the only site of it ever looked up.
+//   phase 2 (thread per row word): one shared-memory union per pair of runs
 //     joined by +y / +z bonds inside the tile (runs already joined through
 //     the previous bit are skipped).
-//   phase 4 (lane per site): find the tile-local root and write the forest
-//     word (root as a global index, local-root marker, cluster draw).
+//   phase 3 (lane per site): find the tile-local root of the site's run
+//     start and write the forest word (root as a global index, local-root
+//     marker, cluster draw).
 //   With MEASURE the row threads also measure the incoming spins (the state
 //   after the previous sweep) from the same bytes and equality masks.
 // k_bonds_xy: XY bonds (lane per site): project on the sweep's mirror axis
@@ -84,7 +86,8 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
 template <int D>
 struct LabelSmem {
   static constexpr int ROWS = Tile<D>::ROWS, NW = kTileThreads / 32;
-  uint32_t par[ROWS * 32];
+  alignas(16) uint32_t par[ROWS * 32];
+  uint32_t srow[ROWS];  // global index of each row word's first site
   // cluster draws of the tile: row r's bytes 4j..4j+3 in word j*(ROWS+1)+r
   // (row-thread stores and lane reads both bank-conflict free)
   uint32_t sdraw[8 * (ROWS + 1)];
@@ -125,6 +128,17 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   const bool draws = (sweep != 0u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+  // every run start is its own parent until the unions (other sites are
+  // never looked up: a site's root is the root of its run start)
+  {
+    uint4* p4 = reinterpret_cast<uint4*>(par);
+#pragma unroll
+    for (int k = 0; k < ROWS * 32 / 4 / kTileThreads; ++k) {
+      const uint32_t t = 4u * (uint32_t)(threadIdx.x + k * kTileThreads);
+      p4[threadIdx.x + k * kTileThreads] = make_uint4(t, t + 1u, t + 2u, t + 3u);
+    }
+  }
+
   // ---- phase 1: bonds, runs and draws of this thread's row word
   const int r = threadIdx.x;
   const int ry = r % TY, rz = r / TY;
@@ -135,6 +149,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   uint32_t X = 0u, Y = 0u, Z = 0u, S = 0u, XW = 0u;
   if (rowv) {
     const uint32_t row = (uint32_t)y + (uint32_t)L * (uint32_t)z;
+    sm.srow[r] = row * (uint32_t)L + (uint32_t)tc.x0;
     const uint32_t g = row * (uint32_t)lat.W + (uint32_t)tc.tx;
     uint32_t A0, A1, A2 = 0u;
     if (FROM_MASK) {
@@ -177,9 +192,9 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
             if (b < nvalid) atomicAdd(&s_hist[(rb.a[b >> 2] >> (8 * (b & 3))) & 0xffu], 1u);
         }
       }
-      A0 = e0 ? (e0 & bernoulli_word(g, sweep, 0, lat.t_bond, lat.key0, lat.key1)) : 0u;
-      A1 = e1 ? (e1 & bernoulli_word(g, sweep, 1, lat.t_bond, lat.key0, lat.key1)) : 0u;
-      if (D == 3) A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, lat.key0, lat.key1)) : 0u;
+      A0 = e0 ? (e0 & bernoulli_word(g, sweep, 0, lat.t_bond, e0, lat.rk)) : 0u;
+      A1 = e1 ? (e1 & bernoulli_word(g, sweep, 1, lat.t_bond, e1, lat.rk)) : 0u;
+      if (D == 3) A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, e2, lat.rk)) : 0u;
       lat.planes[g] = A0;
       lat.planes[plane + g] = A1;
       if (D == 3) lat.planes[2 * plane + g] = A2;
@@ -204,7 +219,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
             const uint32_t i = i0 + (uint32_t)b;
             if ((i >> 2) != cached) {
               cached = i >> 2;
-              w = philox(cached, sweep, kDraw, 0u, lat.key0, lat.key1);
+              w = philox(cached, sweep, kDraw, 0u, lat.rk);
             }
             packed |= draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.dq) << (8 * t);
           }
@@ -217,17 +232,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   sS[r] = S;
   __syncthreads();
 
-  // ---- phase 2: parent of every site = start of its x-run
-#pragma unroll 4
-  for (int k = 0; k < RPW; ++k) {
-    const int rr = warp + NW * k;
-    const uint32_t st = sS[rr];
-    const uint32_t t = (uint32_t)(32 * rr + lane);
-    par[t] = (st != 0u && lane < nvalid) ? (uint32_t)(32 * rr) + run_start(st, lane) : t;
-  }
-  __syncthreads();
-
-  // ---- phase 3: unions of runs joined by in-tile +y / +z bonds
+  // ---- phase 2: unions of runs joined by in-tile +y / +z bonds
   if (rowv) {
     if (Y) {
       const int rn = r + (y1 - y);
@@ -253,22 +258,18 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   }
   __syncthreads();
 
-  // ---- phase 4: forest word of every site
+  // ---- phase 3: forest word of every site
   const uint32_t lr_bit = 1u << lat.sbits;
   const int shift = lat.sbits + 1;
 #pragma unroll 2
   for (int k = 0; k < RPW; ++k) {
     const int rr = warp + NW * k;
-    const int yy = tc.y0 + rr % TY, zz = tc.z0 + rr / TY;
-    if (sS[rr] == 0u || lane >= nvalid) continue;
+    const uint32_t st = sS[rr];
+    if (st == 0u || lane >= nvalid) continue;
     const uint32_t t = (uint32_t)(32 * rr + lane);
-    const uint32_t lr = sfind(par, t);
-    const uint32_t lrow = lr >> 5;
-    const uint32_t gx = (uint32_t)tc.x0 + (lr & 31u);
-    const uint32_t gy = (uint32_t)tc.y0 + lrow % TY;
-    const uint32_t gz = (uint32_t)tc.z0 + lrow / TY;
-    const uint32_t gidx = gx + (uint32_t)L * (gy + (uint32_t)L * gz);
-    const uint32_t i = (uint32_t)(tc.x0 + lane) + (uint32_t)L * ((uint32_t)yy + (uint32_t)L * (uint32_t)zz);
+    const uint32_t lr = sfind(par, (uint32_t)(32 * rr) + run_start(st, lane));
+    const uint32_t gidx = sm.srow[lr >> 5] + (lr & 31u);
+    const uint32_t i = sm.srow[rr] + (uint32_t)lane;
     const uint32_t draw = draws ? (sdraw[(lane >> 2) * (ROWS + 1) + rr] >> (8 * (lane & 3))) & 0xffu : 0u;
     lat.forest[i] = (gidx << shift) | (lr == t ? lr_bit : 0u) | draw;
   }
@@ -285,7 +286,8 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
 }
 
 template <int D, bool FROM_MASK, int MM>
-__global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t sweep, Measure mb) {
+__global__ void __launch_bounds__(kTileThreads, 4) k_label(const __grid_constant__ Lattice lat, uint32_t sweep,
+                                                              const __grid_constant__ Measure mb) {
   __shared__ LabelSmem<D> sm;
   label_tile<D, FROM_MASK, MM>(lat, blockIdx.x, sweep, mb, sm);
 }
@@ -296,19 +298,26 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(Lattice lat, uint32_t
 template <int D>
 __global__ void __launch_bounds__(kTileThreads, 4) k_label_batch(BatchView bv) {
   __shared__ LabelSmem<D> sm;
+  // the member's lattice view is copied to shared memory: the Philox round
+  // keys are read on every round
+  __shared__ Lattice s_lat;
+  static_assert(sizeof(Lattice) % 4 == 0 && sizeof(Lattice) / 4 <= kTileThreads, "lattice copy");
   const uint32_t b = __ldg(&bv.tile_lattice[blockIdx.x]);
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const BatchMember& m = bv.members[b];
+  if (threadIdx.x < sizeof(Lattice) / 4)
+    reinterpret_cast<uint32_t*>(&s_lat)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&m.lat)[threadIdx.x];
+  __syncthreads();
   const uint32_t step = *bv.step;
   const uint32_t sweep = m.sweep0 + step + 1u;
-  if (step == 0u) label_tile<D, false, 0>(m.lat, tile, sweep, m.meas, sm);
-  else if (m.lat.model == kPotts) label_tile<D, false, 2>(m.lat, tile, sweep, m.meas, sm);
-  else label_tile<D, false, 1>(m.lat, tile, sweep, m.meas, sm);
+  if (step == 0u) label_tile<D, false, 0>(s_lat, tile, sweep, m.meas, sm);
+  else if (s_lat.model == kPotts) label_tile<D, false, 2>(s_lat, tile, sweep, m.meas, sm);
+  else label_tile<D, false, 1>(s_lat, tile, sweep, m.meas, sm);
 }
 
 // ---------------------------------------------------------------- XY bonds
 template <int D>
-__global__ void __launch_bounds__(256) k_bonds_xy(Lattice lat, uint32_t sweep) {
+__global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattice lat, uint32_t sweep) {
   __shared__ float s_phi;
   if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
   __syncthreads();
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(256) k_bonds_xy(Lattice lat, uint32_t sweep) {
     uint32_t a = 0u;
     if (x < L) {
       const uint32_t i = (uint32_t)x + (uint32_t)L * row;
-      const uint4 w = philox(i, sweep, kBond, 0u, lat.key0, lat.key1);
+      const uint4 w = philox(i, sweep, kBond, 0u, lat.rk);
       uint32_t jn[3];
       jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
       jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
@@ -358,7 +367,7 @@ __global__ void __launch_bounds__(256) k_bonds_xy(Lattice lat, uint32_t sweep) {
 // sweep's mirror index s; bond (i,d) active iff u(i,d) < t[k_i][k_j] (the
 // table is 0 where x_i x_j <= 0); u(i,d) = word d of Philox(i, sweep, BOND, 0).
 template <int D>
-__global__ void __launch_bounds__(256) k_bonds_clock(Lattice lat, uint32_t sweep) {
+__global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lattice lat, uint32_t sweep) {
   __shared__ uint32_t s_mirror;
   if (threadIdx.x == 0) s_mirror = clock_mirror(lat, sweep);
   __syncthreads();
@@ -377,7 +386,7 @@ __global__ void __launch_bounds__(256) k_bonds_clock(Lattice lat, uint32_t sweep
     uint32_t a = 0u;
     if (x < L) {
       const uint32_t i = (uint32_t)x + (uint32_t)L * row;
-      const uint4 w = philox(i, sweep, kBond, 0u, lat.key0, lat.key1);
+      const uint4 w = philox(i, sweep, kBond, 0u, lat.rk);
       uint32_t jn[3];
       jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
       jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;

@@ -16,9 +16,9 @@ namespace {
 using namespace dev;
 
 template <int MODEL>
-__global__ void __launch_bounds__(256) k_init(Lattice lat) {
+__global__ void __launch_bounds__(256) k_init(const __grid_constant__ Lattice lat) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < lat.N; i += gridDim.x * blockDim.x) {
-    const uint32_t w = philox(i, 0u, kInit, 0u, lat.key0, lat.key1).x;
+    const uint32_t w = philox(i, 0u, kInit, 0u, lat.rk).x;
     if (MODEL == kIsing) {
       static_cast<int8_t*>(lat.spins)[i] = (w >> 31) ? (int8_t)-1 : (int8_t)1;
     } else if (MODEL == kPotts) {
