@@ -31,8 +31,11 @@
  *         is bit (x & 31) of word k of the sequence of i's row word
  *         g = row*W + (x >> 5), word k = word (k & 3) of counter
  *         (g, k_sweep, 1, 8d + k/4).  XY: counter (i, sweep, 1, 0), word d;
- *       2 cluster draws: counter (i >> 2, sweep, 2, 0), word (i & 3) is
- *         the draw w of site i, used when i is the root of its cluster;
+ *       2 cluster draws, used when site i is the root of its cluster:
+ *         Potts with q > 2: w = word (i & 3) of counter (i >> 2, sweep, 2, 0);
+ *         two-state draws (Ising, Potts q = 2, XY, clock): one bit, bit
+ *         (x & 31) of word 0 of counter (g, sweep, 2, 1) for i's row word
+ *         g = row*W + (x >> 5), read as w = bit * 2^31;
  *       3 XY mirror angle: counter (0, sweep, 3, 0), word 0.
  *   - q-state clock model (the paper's discretised XY, Sec. 1 and Sec. 3,
  *     q = 512 there): per sweep a mirror index s = floor(w 2q / 2^32) from

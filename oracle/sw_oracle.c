@@ -37,8 +37,12 @@
  *                      of u(i,d) is bit (x & 31) of the k-th word, the k-th
  *                      word being word (k & 3) of counter (g, k, 1, 8d + k/4).
  *                      XY: counter (i, k, 1, 0), word d -> u(i,d).
- *   purpose 2 (DRAW):  counter (i >> 2, k, 2, 0), word (i & 3) -> the
- *                      cluster draw w(i), used when i is a cluster root.
+ *   purpose 2 (DRAW):  the cluster draw w(i), used when i is a cluster
+ *                      root.  Potts with q > 2: counter (i >> 2, k, 2, 0),
+ *                      word (i & 3).  Two-state draws (Ising, Potts q = 2,
+ *                      XY, clock): one bit, bit (x & 31) of word 0 of
+ *                      counter (g, k, 2, 1) for i's row word g; w(i) is
+ *                      that bit times 2^31.
  *   purpose 3 (AXIS):  counter (0, k, 3, 0), word 0 -> XY mirror angle, or
  *                      the clock model's mirror index.
  *   Clock bonds:       counter (i, k, 1, 0), word d -> u(i,d) (32 bits).
@@ -381,11 +385,19 @@ int64_t oracle_flip(int model, int dim, int L, int q, uint64_t seed, uint32_t sw
   int64_t nclusters = 0;
   uint32_t* root_draw = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
   if (!root_draw) return -1;
+  const int two_state = !(model == OR_POTTS && q > 2);
   for (int64_t r = 0; r < N; ++r) {
     if (labels[r] != r) continue;
     uint32_t w[4];
-    draw4(seed, (uint32_t)(r >> 2), sweep, PURPOSE_DRAW, 0u, w);
-    root_draw[r] = w[r & 3];
+    if (two_state) {
+      const int64_t x = r % L;
+      const int64_t g = (r / L) * row_words(L) + (x >> 5);
+      draw4(seed, (uint32_t)g, sweep, PURPOSE_DRAW, 1u, w);
+      root_draw[r] = ((w[0] >> (x & 31)) & 1u) << 31;
+    } else {
+      draw4(seed, (uint32_t)(r >> 2), sweep, PURPOSE_DRAW, 0u, w);
+      root_draw[r] = w[r & 3];
+    }
     ++nclusters;
   }
   double phi = (model == OR_XY) ? (double)oracle_xy_phi(seed, sweep) : 0.0;

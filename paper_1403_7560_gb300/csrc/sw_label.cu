@@ -6,7 +6,9 @@
 //     spins -- equality of the row with its +x/+y/+z neighbour rows from
 //     byte-lane compares, AND a bit-sliced Bernoulli word per direction
 //     (u < t decided for 32 sites at once from whole Philox words) -- and
-//     the row's cluster draws; or the bonds read from the bit-planes.
+//     the row's cluster draws (one Philox word per row word for two-state
+//     draws, one per four sites for Potts); or the bonds read from the
+//     bit-planes.
 //   Before it, every site is its own parent in the shared-memory forest; an
 //   x-run is represented by its start, the only site of it ever looked up.
 //   phase 2 (thread per row word): one shared-memory union per pair of runs
@@ -88,8 +90,9 @@ struct LabelSmem {
   static constexpr int ROWS = Tile<D>::ROWS, NW = kTileThreads / 32;
   alignas(16) uint32_t par[ROWS * 32];
   uint32_t srow[ROWS];  // global index of each row word's first site
-  // cluster draws of the tile: row r's bytes 4j..4j+3 in word j*(ROWS+1)+r
-  // (row-thread stores and lane reads both bank-conflict free)
+  // cluster draws of the tile: two-state draws, row r's 32 bits in word r;
+  // Potts, row r's bytes 4j..4j+3 in word j*(ROWS+1)+r (row-thread stores
+  // and lane reads both bank-conflict free)
   uint32_t sdraw[8 * (ROWS + 1)];
   uint32_t sX[ROWS], sS[ROWS];
   // Potts histogram: per-warp bins for q <= kSmallQ, shared bins above
@@ -126,6 +129,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   const int nvalid = min(32, L - tc.x0);
   const uint32_t vmask = (nvalid >= 32) ? kFull : ((1u << nvalid) - 1u);
   const bool draws = (sweep != 0u);
+  const bool two_state = lat.dq == 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   // every run start is its own parent until the unions (other sites are
@@ -204,8 +208,11 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
     XW = (tc.x0 == 0 && L <= 32) ? ((A0 >> (L - 1)) & 1u) : 0u;  // wrap inside the word
     Y = (y1 - tc.y0 >= 0 && y1 - tc.y0 < TY) ? A1 : 0u;
     Z = (D == 3 && z1 - tc.z0 >= 0 && z1 - tc.z0 < TZ) ? A2 : 0u;
-    if (draws) {
-      // cluster draw of every site: word (i & 3) of Philox(i >> 2, sweep, DRAW, 0)
+    if (draws && two_state) {
+      // two-state cluster draws: bit (x & 31) of word 0 of Philox(g, sweep, DRAW, 1)
+      sdraw[r] = philox(g, sweep, kDraw, 1u, lat.rk).x;
+    } else if (draws) {
+      // Potts cluster draw of every site: word (i & 3) of Philox(i >> 2, sweep, DRAW, 0)
       const uint32_t i0 = row * (uint32_t)L + (uint32_t)tc.x0;
       uint32_t cached = 0xffffffffu;
       uint4 w = make_uint4(0u, 0u, 0u, 0u);
@@ -270,7 +277,9 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
     const uint32_t lr = sfind(par, (uint32_t)(32 * rr) + run_start(st, lane));
     const uint32_t gidx = sm.srow[lr >> 5] + (lr & 31u);
     const uint32_t i = sm.srow[rr] + (uint32_t)lane;
-    const uint32_t draw = draws ? (sdraw[(lane >> 2) * (ROWS + 1) + rr] >> (8 * (lane & 3))) & 0xffu : 0u;
+    const uint32_t draw = !draws ? 0u
+                          : two_state ? (sdraw[rr] >> lane) & 1u
+                                      : (sdraw[(lane >> 2) * (ROWS + 1) + rr] >> (8 * (lane & 3))) & 0xffu;
     lat.forest[i] = (gidx << shift) | (lr == t ? lr_bit : 0u) | draw;
   }
   if (MEASURE) {
