@@ -84,26 +84,29 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
 // spins (the state after sweep - 1): M and E from the row words' equality
 // masks and the Potts histogram, added to the measurement slots (the flip
 // kernel of this sweep writes the record of sweep - 1).  MM = 0: none.
-// Shared memory of one tile's labeling.
-template <int D>
+// Shared memory of one tile's labeling in measurement mode MM (the Potts
+// draw words and histograms only where Potts lattices can run).
+template <int D, int MM>
 struct LabelSmem {
   static constexpr int ROWS = Tile<D>::ROWS, NW = kTileThreads / 32;
+  static constexpr int kDrawWords = (MM == 1 ? 1 : 8) * (ROWS + 1);
+  static constexpr int kHist = MM == 2 ? 256 : 1, kWHist = MM == 2 ? NW * kSmallQ : 1;
   alignas(16) uint32_t par[ROWS * 32];
   uint32_t srow[ROWS];  // global index of each row word's first site
   // cluster draws of the tile: two-state draws, row r's 32 bits in word r;
   // Potts, row r's bytes 4j..4j+3 in word j*(ROWS+1)+r (row-thread stores
   // and lane reads both bank-conflict free)
-  uint32_t sdraw[8 * (ROWS + 1)];
+  uint32_t sdraw[kDrawWords];
   uint32_t sX[ROWS], sS[ROWS];
   // Potts histogram: per-warp bins for q <= kSmallQ, shared bins above
-  unsigned int s_hist[256];
-  unsigned int s_whist[NW * kSmallQ];
+  unsigned int s_hist[kHist];
+  unsigned int s_whist[kWHist];
   long long s_red[NW];
 };
 
-template <int D, bool FROM_MASK, int MM>
+template <int D, bool FROM_MASK, int MM, class Smem>
 __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, uint32_t sweep,
-                                           const Measure& mb, LabelSmem<D>& sm) {
+                                           const Measure& mb, Smem& sm) {
   constexpr bool MEASURE = MM != 0;
   constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ, ROWS = Tile<D>::ROWS;
   constexpr int NW = kTileThreads / 32, RPW = ROWS / NW;
@@ -295,9 +298,9 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
 }
 
 template <int D, bool FROM_MASK, int MM>
-__global__ void __launch_bounds__(kTileThreads, 4) k_label(const __grid_constant__ Lattice lat, uint32_t sweep,
+__global__ void __launch_bounds__(kTileThreads, 5) k_label(const __grid_constant__ Lattice lat, uint32_t sweep,
                                                               const __grid_constant__ Measure mb) {
-  __shared__ LabelSmem<D> sm;
+  __shared__ LabelSmem<D, MM> sm;
   label_tile<D, FROM_MASK, MM>(lat, blockIdx.x, sweep, mb, sm);
 }
 
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label(const __grid_constant
 // incoming state of its lattice (the record of the previous sweep).
 template <int D>
 __global__ void __launch_bounds__(kTileThreads, 4) k_label_batch(BatchView bv) {
-  __shared__ LabelSmem<D> sm;
+  __shared__ LabelSmem<D, 2> sm;
   // the member's lattice view is copied to shared memory: the Philox round
   // keys are read on every round
   __shared__ Lattice s_lat;
