@@ -116,7 +116,7 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
 }
 
 template <int D>
-__global__ void __launch_bounds__(kTileThreads, 4) k_merge(Lattice lat) {
+__global__ void __launch_bounds__(kTileThreads, 8) k_merge(Lattice lat) {
   __shared__ MergeSmem<D> sm;
   merge_tile<D>(lat, blockIdx.x, sm);
 }
@@ -159,7 +159,7 @@ __device__ __forceinline__ void compress_tile(const Lattice& lat, uint32_t t) {
 // word, so that every site is at most two loads away from its cluster's
 // draw.  Block 0 first writes the record of the previous measured sweep,
 // from the sums its successor's labeling kernel left behind.
-__global__ void __launch_bounds__(kFlipThreads, 4) k_compress(Lattice lat, Measure mb, uint32_t finalize) {
+__global__ void __launch_bounds__(kFlipThreads, 8) k_compress(Lattice lat, Measure mb, uint32_t finalize) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
   if (finalize != 0u && blockIdx.x == 0) finalize_record<kFlipWarps>(lat, mb, finalize, s_red, s_rd);
