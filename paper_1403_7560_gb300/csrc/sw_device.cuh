@@ -191,6 +191,40 @@ __device__ __forceinline__ uint32_t gfind(uint32_t* f, uint32_t x, int shift, ui
   return x;
 }
 
+// The roots of a and b, the two walks advanced in lockstep so that their
+// loads are in flight together (path halving as in gfind).
+__device__ __forceinline__ void gfind2(uint32_t* f, uint32_t& a, uint32_t& b, int shift, uint32_t marker) {
+  bool da = false, db = false;
+  for (int it = 0; it < (1 << 22); ++it) {
+    const uint32_t pa = da ? a : __ldcg(&f[a]) >> shift;
+    const uint32_t pb = db ? b : __ldcg(&f[b]) >> shift;
+    da = da || pa == a;
+    db = db || pb == b;
+    if (da && db) return;
+    const uint32_t ga = da ? a : __ldcg(&f[pa]) >> shift;
+    const uint32_t gb = db ? b : __ldcg(&f[pb]) >> shift;
+    if (!da) {
+      if (ga == pa) {
+        a = pa;
+        da = true;
+      } else {
+        __stcg(&f[a], (ga << shift) | marker);
+        a = ga;
+      }
+    }
+    if (!db) {
+      if (gb == pb) {
+        b = pb;
+        db = true;
+      } else {
+        __stcg(&f[b], (gb << shift) | marker);
+        b = gb;
+      }
+    }
+    if (da && db) return;
+  }
+}
+
 // Joins the trees of a and b; returns the root that was hooked under the
 // other tree (each root is hooked at most once), or 0xffffffff if the two
 // were already one tree.
@@ -198,8 +232,7 @@ __device__ __forceinline__ uint32_t gunion(uint32_t* f, uint32_t a, uint32_t b, 
   const int shift = sb + 1;
   const uint32_t marker = 1u << sb;
   for (int it = 0; it < (1 << 20); ++it) {
-    a = gfind(f, a, shift, marker);
-    b = gfind(f, b, shift, marker);
+    gfind2(f, a, b, shift, marker);
     if (a == b) return 0xffffffffu;
     if (a < b) {
       const uint32_t t = a;
