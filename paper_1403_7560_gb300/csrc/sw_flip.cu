@@ -326,7 +326,7 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
   if (g > kFlipBlocks) g = kFlipBlocks;
   if (g == 0) g = 1;
   const unsigned ntiles = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  k_compress<<<ntiles < kFlipBlocks ? ntiles : kFlipBlocks, kFlipThreads, 0, st>>>(lat, m, finalize);
+  k_compress<<<ntiles, kFlipThreads, 0, st>>>(lat, m, finalize);
   if (model == kIsing) k_apply<kIsing><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   else if (model == kPotts) k_apply<kPotts><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
   else if (model == kClock) k_apply<kClock><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
