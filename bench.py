@@ -53,6 +53,10 @@ WORKLOAD = {"workload": "3D Ising SW sweep, simple cubic L=256 periodic, K=0.221
 # The merge touches only tile faces and is given per face bond instead.
 KERNEL_BYTES_PER_SITE = {"bond_label": 1 + 3 / 8 + 4, "merge": None, "flip": 4 + 1, "measure": 1}
 PHASES = ["bond_label", "merge", "flip", "measure"]
+# DRAM bytes (read + write) of one launch of the dominant kernel, k_label
+# with measurement, from one ncu capture of this build (cold cache; see
+# profiles/sweep_kernels_ising3d_L256.md); None once that kernel changes.
+KERNEL_DRAM_BYTES = {"bond_label": 16.851968e6 + 14.457088e6}
 # kernels one measured sweep launches: k_label (bonds + tile labels + the
 # previous sweep's measurement), k_merge, k_compress, k_apply
 KERNELS_PER_SWEEP = 4
@@ -311,8 +315,10 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
             "roofline": {"bound": "hbm", "kernel": PHASES[dom], "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": KERNEL_DRAM_BYTES.get(PHASES[dom]),
                          "peak_source": f"{peak_kind} hbm_gbs",
+                         "limiter": "instruction issue (ncu: 69% issue active, 5.3 warp instr/site)",
                          "bytes_per_site": bps},
             "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
             "update_only": {"value": update_only, "unit": UNIT},
