@@ -211,6 +211,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# The other single-lattice workloads of the measurement plan, timed briefly
+# beside the headline (CUDA events per measured sweep, L2 flushed between
+# sweeps): 3D XY L=256 at K=0.4541652 (seed 1002) and the small 2D Ising
+# L=64 lattice at T=2.269185 (seed 1000), which is launch-latency bound.
+OTHER_WORKLOADS = [
+    ("xy3d_L256", 2, 3, 256, 2, 1.0 / 0.4541652, 1002, 20, 50),
+    ("ising2d_L64", 0, 2, 64, 2, 2.269185, 1000, 200, 500),
+]
+
+
+def other_workloads(sw, stream, flush, rank):
+    import torch
+    out = {}
+    for name, model, dim, L_, q, T_, seed, discard, steps in OTHER_WORKLOADS:
+        h = sw.sw_create(model, dim, L_, q, T_, seed + rank)
+        sw.sw_set_stream(h, stream.cuda_stream)
+        sw.sw_discard(h, discard)
+        sw.sw_sweep(h, 3)
+        sw.sw_measure(h)
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sw.sw_sweep(h, 1)
+            b.record(stream)
+            flush.fill_(k & 0xff)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(x.elapsed_time(y) for x, y in ts)
+        mom = sw.sw_measure(h)
+        n = L_ ** dim
+        out[name] = {"value": n / (ms * 1e6), "unit": UNIT, "ms_per_step": ms, "ns_per_site": ms * 1e6 / n,
+                     "steps": steps, "sites": n, "T": T_, "e_per_spin": mom["e_per_spin"]}
+        sw.sw_destroy(h)
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_1403_7560_gb300 import build, sw
@@ -286,6 +325,8 @@ def run_gpu(args):
                 "label_equivalence_iterations": statistics.mean(lab_it),
                 "speedup": statistics.mean(lab_le) / statistics.mean(lab_uf)}
 
+    secondary = other_workloads(sw, stream, flush, rank)
+
     # end to end through the C ABI with pinned host buffers
     host_in = torch.empty(N_SITES, dtype=torch.int8, pin_memory=True).numpy()
     host_out = torch.empty(N_SITES, dtype=torch.int8, pin_memory=True).numpy()
@@ -323,6 +364,7 @@ def run_gpu(args):
             "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
             "update_only": {"value": update_only, "unit": UNIT},
             "labeling": labeling,
+            "other_workloads": secondary,
             "b_ref": {"bytes_per_site": B_REF, "GBps": value * B_REF, "frac": value * B_REF / peak},
             "gpu_launches": KERNELS_PER_SWEEP * args.steps,
             "clocks": clk,

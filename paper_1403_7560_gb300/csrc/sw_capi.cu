@@ -133,14 +133,27 @@ int check_device_error(sw_handle* h) {
 
 // Step (1) and the tile half of step (2): Ising/Potts bonds are drawn inside
 // the labeling kernel, which also measures the incoming state when the
-// previous sweep's record is pending; XY bonds come from their own kernel.
-// Sets *finalize to the pending sweep whose record the flip kernel of this
-// sweep must write (0 if none).
+// previous sweep's record is pending; XY and clock bonds come from their own
+// kernel (the XY one measures the pending state too).  Sets *finalize to
+// the pending sweep whose record the flip kernel of this sweep must write
+// (0 if none).
 cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k, uint32_t* finalize) {
   *finalize = 0u;
   if (h->model == SW_XY || h->model == SW_CLOCK) {
-    cudaError_t e = (h->model == SW_XY) ? swgb::launch_bonds_xy(h->lat, k, h->stream)
-                                        : swgb::launch_bonds_clock(h->lat, k, h->stream);
+    cudaError_t e;
+    if (h->model == SW_XY) {
+      const swgb::Measure* m = nullptr;
+      if (h->pending) {
+        *finalize = (uint32_t)h->pending;
+        h->pending = 0;
+        m = &h->meas;
+      }
+      int blocks = 0;
+      e = swgb::launch_bonds_xy(h->lat, k, m, &blocks, h->stream);
+      if (m) h->meas.xy_blocks = blocks;
+    } else {
+      e = swgb::launch_bonds_clock(h->lat, k, h->stream);
+    }
     if (e != cudaSuccess) return e;
     return swgb::launch_label(h->lat, k, true, h->stream);
   }
@@ -167,8 +180,9 @@ cudaError_t swgb::flush_pending(sw_handle* h) {
 namespace {
 using swgb::flush_pending;
 
-// One sweep; Ising/Potts leave their measurement pending (it is taken from
-// the next sweep's labeling kernel or by flush_pending), XY measures at once.
+// One sweep; Ising/Potts/XY leave their measurement pending (it is taken
+// from the next sweep's bond kernel or by flush_pending), clock measures at
+// once.
 cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   cudaError_t e = cudaSuccess;
   uint32_t finalize = 0u;
@@ -180,7 +194,7 @@ cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas, measure, finalize, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->stream);
   if (e == cudaSuccess && measure) {
-    if (h->model == SW_XY || h->model == SW_CLOCK) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
+    if (h->model == SW_CLOCK) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
     else h->pending = k;
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], h->stream);

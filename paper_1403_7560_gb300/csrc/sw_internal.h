@@ -112,7 +112,10 @@ void set_last_error(const std::string& msg);
 
 cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
 // Bonds of the XY model (lane per site) into the bit-planes.
-cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, cudaStream_t st);
+// XY bonds of `sweep`; with m != nullptr the kernel also measures the
+// incoming state into m's XY partials, one per block (*blocks = grid).
+cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, const Measure* m, int* blocks,
+                            cudaStream_t st);
 // Bonds of the clock model (lane per site, table thresholds).
 cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, cudaStream_t st);
 // Tile labels (+ Ising/Potts bonds when from_mask is false; cluster draws

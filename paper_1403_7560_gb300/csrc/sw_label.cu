@@ -19,8 +19,10 @@
 //     marker, cluster draw).
 //   With MEASURE the row threads also measure the incoming spins (the state
 //   after the previous sweep) from the same bytes and equality masks.
-// k_bonds_xy: XY bonds (lane per site): project on the sweep's mirror axis
-//   and test the embedded-Ising probability; ballot into the bit-planes.
+// k_bonds_xy: XY bonds: project on the sweep's mirror axis (once per site,
+//   through a shared-memory block with halo) and test the embedded-Ising
+//   probability; ballot into the bit-planes; optionally measure the
+//   incoming state from the same projections.
 #include "sw_device.cuh"
 
 namespace swgb {
@@ -328,48 +330,109 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label_batch(BatchView bv) {
 }
 
 // ---------------------------------------------------------------- XY bonds
+// One CTA per 32 x BY (x BZ) block of sites, grid-strided over the blocks.
+// The projections (x, y) = (cos, sin)(theta - phi) on the sweep's mirror
+// axis are computed once per site of the block and its +x/+y/+z halo into
+// shared memory; bond (i,d) is active iff x_i x_j > 0 and the uniform of
+// word d of Philox(i, sweep, BOND, 0) is below 1 - exp(-2K x_i x_j); warps
+// ballot their rows into the bit-planes.  With MEASURE the same values
+// measure the incoming state (the state after sweep - 1): sum x, sum y and
+// the bond energies x_i x_j + y_i y_j (cos(theta_i - theta_j), invariant
+// under the rotation by phi) in float per thread, then double per block;
+// the block's (sum cos theta, sum sin theta, E) partial, rotated back by
+// phi, goes to slot blockIdx of the XY partials.
 template <int D>
-__global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattice lat, uint32_t sweep) {
+struct XYBlock;
+template <>
+struct XYBlock<2> {
+  static constexpr int BY = 128, BZ = 1;
+};
+template <>
+struct XYBlock<3> {
+  static constexpr int BY = 16, BZ = 8;
+};
+
+template <int D, bool MEASURE>
+__global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattice lat, uint32_t sweep,
+                                                   const __grid_constant__ Measure mb) {
+  constexpr int BY = XYBlock<D>::BY, BZ = XYBlock<D>::BZ;
+  constexpr int HX = 33, HY = BY + 1, HZ = (D == 3) ? BZ + 1 : 1, NBOX = HX * HY * HZ;
+  constexpr int NW = 256 / 32;
+  __shared__ float2 sv[NBOX];
   __shared__ float s_phi;
+  __shared__ double s_rd[NW];
   if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
   __syncthreads();
   const float phi = s_phi;
-  const int L = lat.L, lane = threadIdx.x & 31;
-  const uint32_t nwords = lat.R * (uint32_t)lat.W;
-  const uint32_t plane = nwords;
+  const int L = lat.L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t plane = lat.R * (uint32_t)lat.W;
   const float* th = static_cast<const float*>(lat.spins);
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t g = gw; g < nwords; g += nw) {
-    const uint32_t row = g / (uint32_t)lat.W, xw = g % (uint32_t)lat.W;
-    const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
-    const int x = (int)(32 * xw) + lane;
-    uint32_t a = 0u;
-    if (x < L) {
-      const uint32_t i = (uint32_t)x + (uint32_t)L * row;
-      const uint4 w = philox(i, sweep, kBond, 0u, lat.rk);
-      uint32_t jn[3];
-      jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
-      jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
-      jn[2] = (D == 3) ? ((z + 1 == (uint32_t)L) ? i - z * L * L : i + (uint32_t)L * L) : 0u;
-      const float xi = cosf(__fsub_rn(th[i], phi));
+  const uint32_t nbx = (uint32_t)lat.W, nby = (uint32_t)((L + BY - 1) / BY);
+  const uint32_t nbz = (D == 3) ? (uint32_t)((L + BZ - 1) / BZ) : 1u;
+  const uint32_t nblocks = nbx * nby * nbz;
+  float fx = 0.f, fy = 0.f, fe = 0.f;
+  for (uint32_t t = blockIdx.x; t < nblocks; t += gridDim.x) {
+    const int x0 = 32 * (int)(t % nbx), y0 = BY * (int)((t / nbx) % nby), z0 = BZ * (int)(t / (nbx * nby));
+    const int nx = min(32, L - x0), ny = min(BY, L - y0), nz = (D == 3) ? min(BZ, L - z0) : 1;
+    __syncthreads();  // the previous block's values are no longer read
+    for (int e = threadIdx.x; e < NBOX; e += 256) {
+      const int xx = e % HX, r = e / HX, yy = r % HY, zz = r / HY;
+      if (xx > nx || yy > ny || zz > nz) continue;  // beyond the valid sites and their halo
+      int gx = x0 + xx, gy = y0 + yy, gz = (D == 3) ? z0 + zz : 0;
+      if (gx >= L) gx -= L;
+      if (gy >= L) gy -= L;
+      if (gz >= L) gz -= L;
+      float sn, cs;
+      sincosf(__fsub_rn(__ldg(&th[(uint32_t)gx + (uint32_t)L * ((uint32_t)gy + (uint32_t)L * (uint32_t)gz)]), phi),
+              &sn, &cs);
+      sv[e] = make_float2(cs, sn);
+    }
+    __syncthreads();
+    for (int rr = warp; rr < BY * BZ; rr += NW) {
+      const int yy = rr % BY, zz = rr / BY;
+      const bool rowv = yy < ny && zz < nz;
+      uint32_t a = 0u;
+      if (rowv && lane < nx) {
+        const uint32_t y = (uint32_t)(y0 + yy), z = (uint32_t)(z0 + zz);
+        const uint32_t i = (uint32_t)(x0 + lane) + (uint32_t)L * (y + (uint32_t)L * z);
+        const uint4 w = philox(i, sweep, kBond, 0u, lat.rk);
+        const int c = lane + HX * (yy + HY * zz);
+        const float2 si = sv[c];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const float2 sj = sv[c + (d == 0 ? 1 : d == 1 ? HX : HX * HY)];
+          const float prod = __fmul_rn(si.x, sj.x);
+          bool act = false;
+          if (prod > 0.0f) {
+            const float p = -expm1f(-__fmul_rn(lat.twoK, prod));
+            const float u = __fmul_rn((float)(word_of(w, d) >> 8), 0x1p-24f);
+            act = u < p;
+          }
+          a |= (uint32_t)act << d;
+          if (MEASURE) fe = __fadd_rn(fe, __fadd_rn(prod, __fmul_rn(si.y, sj.y)));
+        }
+        if (MEASURE) {
+          fx = __fadd_rn(fx, si.x);
+          fy = __fadd_rn(fy, si.y);
+        }
+      }
+      const uint32_t row = (uint32_t)(y0 + yy) + (uint32_t)L * (uint32_t)(z0 + zz);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const float xj = cosf(__fsub_rn(th[jn[d]], phi));
-        const float prod = __fmul_rn(xi, xj);
-        bool act = false;
-        if (prod > 0.0f) {
-          const float p = -expm1f(-__fmul_rn(lat.twoK, prod));
-          const float u = __fmul_rn((float)(word_of(w, d) >> 8), 0x1p-24f);
-          act = u < p;
-        }
-        a |= (uint32_t)act << d;
+        const uint32_t bal = __ballot_sync(kFull, (a >> d) & 1u);
+        if (rowv && lane == d) lat.planes[d * plane + row * (uint32_t)lat.W + (uint32_t)(x0 >> 5)] = bal;
       }
     }
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const uint32_t bal = __ballot_sync(kFull, (a >> d) & 1u);
-      if (lane == d) lat.planes[d * plane + g] = bal;
+  }
+  if (MEASURE) {
+    const double sx = block_combine<NW>((double)warp_sum(fx), s_rd);
+    const double sy = block_combine<NW>((double)warp_sum(fy), s_rd);
+    const double se = block_combine<NW>((double)warp_sum(fe), s_rd);
+    if (threadIdx.x == 0) {
+      const double c = cos((double)phi), sn = sin((double)phi);
+      mb.part_d[3 * blockIdx.x + 0] = __dsub_rn(__dmul_rn(c, sx), __dmul_rn(sn, sy));
+      mb.part_d[3 * blockIdx.x + 1] = __dadd_rn(__dmul_rn(sn, sx), __dmul_rn(c, sy));
+      mb.part_d[3 * blockIdx.x + 2] = -se;
     }
   }
 }
@@ -473,12 +536,22 @@ cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Meas
   return cudaGetLastError();
 }
 
-cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, cudaStream_t st) {
-  const uint32_t words = lat.R * (uint32_t)lat.W;
-  unsigned g = (words + 7u) / 8u;
-  if (g > 4096u) g = 4096u;
-  if (lat.dim == 2) k_bonds_xy<2><<<g, 256, 0, st>>>(lat, sweep);
-  else k_bonds_xy<3><<<g, 256, 0, st>>>(lat, sweep);
+cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, const Measure* m, int* blocks,
+                            cudaStream_t st) {
+  const uint32_t ny = (uint32_t)((lat.L + XYBlock<3>::BY - 1) / XYBlock<3>::BY);
+  const uint32_t nb = (lat.dim == 2)
+                          ? (uint32_t)lat.W * (uint32_t)((lat.L + XYBlock<2>::BY - 1) / XYBlock<2>::BY)
+                          : (uint32_t)lat.W * ny * (uint32_t)((lat.L + XYBlock<3>::BZ - 1) / XYBlock<3>::BZ);
+  const unsigned g = nb < (uint32_t)kMeasureBlocks ? (nb ? nb : 1u) : (unsigned)kMeasureBlocks;
+  const Measure none{};
+  if (lat.dim == 2) {
+    if (m) k_bonds_xy<2, true><<<g, 256, 0, st>>>(lat, sweep, *m);
+    else k_bonds_xy<2, false><<<g, 256, 0, st>>>(lat, sweep, none);
+  } else {
+    if (m) k_bonds_xy<3, true><<<g, 256, 0, st>>>(lat, sweep, *m);
+    else k_bonds_xy<3, false><<<g, 256, 0, st>>>(lat, sweep, none);
+  }
+  if (blocks) *blocks = (int)g;
   return cudaGetLastError();
 }
 
