@@ -442,7 +442,9 @@ def run_batch(args):
             "serial": {"value": v_serial, "unit": UNIT, "steps": k_serial,
                        "note": "each lattice alone with sw_sweep, one after another"},
             "speedup_vs_serial": v_batch / v_serial,
-            "gpu_launches": 5 * args.steps, "clocks": clk}
+            # per step: labels of the Ising tiles and of the Potts tiles,
+            # merge, compression, apply, step counter
+            "gpu_launches": 6 * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

@@ -33,6 +33,7 @@ struct sw_batch {
   size_t cap_tiles = 0;
   uint32_t* d_step = nullptr;
   uint32_t ntiles = 0;
+  uint32_t ising_tiles = 0;           // the tile map lists the Ising members' tiles first
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev = nullptr;
 };
@@ -90,13 +91,17 @@ int rebuild(sw_batch* b) {
   }
   std::vector<uint32_t> lat(ntiles), idx(ntiles);
   size_t t = 0;
-  for (size_t m = 0; m < b->members.size(); ++m) {
-    const sw_handle* h = b->members[m];
-    const uint32_t n = (uint32_t)((size_t)h->lat.ntx * h->lat.nty * h->lat.ntz);
-    for (uint32_t k = 0; k < n; ++k, ++t) {
-      lat[t] = (uint32_t)m;
-      idx[t] = k;
+  for (int pass = 0; pass < 2; ++pass) {  // Ising members' tiles, then Potts
+    for (size_t m = 0; m < b->members.size(); ++m) {
+      const sw_handle* h = b->members[m];
+      if ((h->model == SW_POTTS) != (pass == 1)) continue;
+      const uint32_t n = (uint32_t)((size_t)h->lat.ntx * h->lat.nty * h->lat.ntz);
+      for (uint32_t k = 0; k < n; ++k, ++t) {
+        lat[t] = (uint32_t)m;
+        idx[t] = k;
+      }
     }
+    if (pass == 0) b->ising_tiles = (uint32_t)t;
   }
   if (ntiles) {
     if ((e = cudaMemcpy(b->d_tiles, lat.data(), ntiles * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -111,7 +116,7 @@ int rebuild(sw_batch* b) {
     const BatchView v = view(b);
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t le = swgb::launch_label_batch(v, b->dim, b->ntiles, b->stream);
+      cudaError_t le = swgb::launch_label_batch(v, b->dim, b->ising_tiles, b->ntiles - b->ising_tiles, b->stream);
       if (le == cudaSuccess) le = swgb::launch_merge_batch(v, b->dim, b->ntiles, b->stream);
       if (le == cudaSuccess) le = swgb::launch_flip_batch(v, b->dim, b->ntiles, b->stream);
       e = cudaStreamEndCapture(b->stream, &g);

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_merge(Lattice lat) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kTileThreads, 4) k_merge_batch(BatchView bv) {
+__global__ void __launch_bounds__(kTileThreads, 8) k_merge_batch(BatchView bv) {
   __shared__ MergeSmem<D> sm;
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   merge_tile<D>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kFlipThreads, 8) k_compress(Lattice lat, Measu
 
 // Batch: one CTA per member tile; the CTA of each member's tile 0 first
 // writes that member's previous record (every step after the first).
-__global__ void __launch_bounds__(kFlipThreads, 4) k_compress_batch(BatchView bv) {
+__global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];

@@ -139,7 +139,10 @@ cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st)
 
 // Batched phases: one launch over every tile of every member (Ising/Potts,
 // one dimension), then the step counter advances.
-cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
+// The tile map lists the Ising members' tiles first (ising_tiles of them),
+// then the Potts members' tiles.
+cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ising_tiles, uint32_t potts_tiles,
+                               cudaStream_t st);
 cudaError_t launch_merge_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
 cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
 

@@ -91,7 +91,8 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
 template <int D, int MM>
 struct LabelSmem {
   static constexpr int ROWS = Tile<D>::ROWS, NW = kTileThreads / 32;
-  static constexpr int kDrawWords = (MM == 1 ? 1 : 8) * (ROWS + 1);
+  static constexpr bool kPottsDraws = MM != 1;  // MM 1: Ising only (two-state draws)
+  static constexpr int kDrawWords = (kPottsDraws ? 8 : 1) * (ROWS + 1);
   static constexpr int kHist = MM == 2 ? 256 : 1, kWHist = MM == 2 ? NW * kSmallQ : 1;
   alignas(16) uint32_t par[ROWS * 32];
   uint32_t srow[ROWS];  // global index of each row word's first site
@@ -216,7 +217,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
     if (draws && two_state) {
       // two-state cluster draws: bit (x & 31) of word 0 of Philox(g, sweep, DRAW, 1)
       sdraw[r] = philox(g, sweep, kDraw, 1u, lat.rk).x;
-    } else if (draws) {
+    } else if (draws && Smem::kPottsDraws) {
       // Potts cluster draw of every site: word (i & 3) of Philox(i >> 2, sweep, DRAW, 0)
       const uint32_t i0 = row * (uint32_t)L + (uint32_t)tc.x0;
       uint32_t cached = 0xffffffffu;
@@ -283,8 +284,9 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
     const uint32_t gidx = sm.srow[lr >> 5] + (lr & 31u);
     const uint32_t i = sm.srow[rr] + (uint32_t)lane;
     const uint32_t draw = !draws ? 0u
-                          : two_state ? (sdraw[rr] >> lane) & 1u
-                                      : (sdraw[(lane >> 2) * (ROWS + 1) + rr] >> (8 * (lane & 3))) & 0xffu;
+                          : (two_state || !Smem::kPottsDraws)
+                              ? (sdraw[rr] >> lane) & 1u
+                              : (sdraw[(lane >> 2) * (ROWS + 1) + rr] >> (8 * (lane & 3))) & 0xffu;
     lat.forest[i] = (gidx << shift) | (lr == t ? lr_bit : 0u) | draw;
   }
   if (MEASURE) {
@@ -308,16 +310,18 @@ __global__ void __launch_bounds__(kTileThreads, 5) k_label(const __grid_constant
 
 // Ising/Potts lattices of a batch, one tile per CTA; sweep numbers come from
 // the batch step counter, and every step after the first also measures the
-// incoming state of its lattice (the record of the previous sweep).
-template <int D>
-__global__ void __launch_bounds__(kTileThreads, 4) k_label_batch(BatchView bv) {
-  __shared__ LabelSmem<D, 2> sm;
+// incoming state of its lattice (the record of the previous sweep).  The
+// tile map lists the Ising members' tiles first: they run in one launch
+// with the two-state layout (five CTAs per SM), the Potts tiles in another.
+template <int D, bool POTTS>
+__global__ void __launch_bounds__(kTileThreads, POTTS ? 4 : 5) k_label_batch(BatchView bv, uint32_t first) {
+  __shared__ LabelSmem<D, POTTS ? 2 : 1> sm;
   // the member's lattice view is copied to shared memory: the Philox round
   // keys are read on every round
   __shared__ Lattice s_lat;
   static_assert(sizeof(Lattice) % 4 == 0 && sizeof(Lattice) / 4 <= kTileThreads, "lattice copy");
-  const uint32_t b = __ldg(&bv.tile_lattice[blockIdx.x]);
-  const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
+  const uint32_t b = __ldg(&bv.tile_lattice[first + blockIdx.x]);
+  const uint32_t tile = __ldg(&bv.tile_index[first + blockIdx.x]);
   const BatchMember& m = bv.members[b];
   if (threadIdx.x < sizeof(Lattice) / 4)
     reinterpret_cast<uint32_t*>(&s_lat)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&m.lat)[threadIdx.x];
@@ -325,8 +329,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_label_batch(BatchView bv) {
   const uint32_t step = *bv.step;
   const uint32_t sweep = m.sweep0 + step + 1u;
   if (step == 0u) label_tile<D, false, 0>(s_lat, tile, sweep, m.meas, sm);
-  else if (s_lat.model == kPotts) label_tile<D, false, 2>(s_lat, tile, sweep, m.meas, sm);
-  else label_tile<D, false, 1>(s_lat, tile, sweep, m.meas, sm);
+  else label_tile<D, false, POTTS ? 2 : 1>(s_lat, tile, sweep, m.meas, sm);
 }
 
 // ---------------------------------------------------------------- XY bonds
@@ -516,9 +519,16 @@ cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
-  if (dim == 2) k_label_batch<2><<<ntiles, kTileThreads, 0, st>>>(bv);
-  else k_label_batch<3><<<ntiles, kTileThreads, 0, st>>>(bv);
+cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ising_tiles, uint32_t potts_tiles,
+                               cudaStream_t st) {
+  if (ising_tiles) {
+    if (dim == 2) k_label_batch<2, false><<<ising_tiles, kTileThreads, 0, st>>>(bv, 0u);
+    else k_label_batch<3, false><<<ising_tiles, kTileThreads, 0, st>>>(bv, 0u);
+  }
+  if (potts_tiles) {
+    if (dim == 2) k_label_batch<2, true><<<potts_tiles, kTileThreads, 0, st>>>(bv, ising_tiles);
+    else k_label_batch<3, true><<<potts_tiles, kTileThreads, 0, st>>>(bv, ising_tiles);
+  }
   return cudaGetLastError();
 }
 
