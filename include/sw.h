@@ -269,6 +269,35 @@ size_t sw_batch_size(sw_batch* b);
 size_t sw_device_bytes(int model, int dim, int L, int q);
 
 /* ------------------------------------------------------------------------
+ * Asynchronous host I/O.  The paper has no counterpart (it times sweeps on a
+ * resident lattice); a loop that streams states in and results out uses
+ * these calls so that the transfers overlap the sweeps.  Host buffers must
+ * be page-locked (cudaHostAlloc / pinned) and stay valid, and for uploads
+ * unchanged, until sw_wait_io or sw_sync returns.  The handle creates two
+ * copy streams and two device buffers of sw_spin_bytes on first use (not
+ * counted by sw_device_bytes).  Not available for a lattice in a batch
+ * (SW_ERR_BAD_ARG).
+ *
+ * sw_set_spins_async(h, host, bytes)  enqueues the upload of a new state;
+ *     sweeps enqueued afterwards start from it.  The measurement pending on
+ *     the replaced state is taken first, as in sw_set_spins.
+ * sw_get_spins_async(h, host, bytes)  enqueues the download of the state
+ *     after the sweeps enqueued so far (a device-side snapshot is taken on
+ *     the handle's stream, so later sweeps do not wait for the transfer).
+ * sw_get_record_async(h, sweep, host) enqueues the download of the record of
+ *     a measured sweep (1 <= sweep <= sw_sweep_counter and among the last
+ *     sw_series_capacity sweeps, else SW_ERR_RANGE) into one sw_record; the
+ *     record's sweep field identifies it (a sweep that was not measured
+ *     leaves another sweep's record in its slot).
+ * sw_wait_io(h)  waits for every enqueued transfer and sweep of the handle.
+ * Errors: SW_ERR_BAD_ARG (NULL, wrong size, batch member), SW_ERR_RANGE,
+ * SW_ERR_CUDA (message in sw_last_error). */
+int sw_set_spins_async(sw_handle* h, const void* host, size_t bytes);
+int sw_get_spins_async(sw_handle* h, void* host, size_t bytes);
+int sw_get_record_async(sw_handle* h, uint64_t sweep, sw_record* host);
+int sw_wait_io(sw_handle* h);
+
+/* ------------------------------------------------------------------------
  * Labeling without device allocation.  The paper has no counterpart: this
  * serves callers that may not allocate device memory themselves, such as a
  * plugin inside a host framework that owns every device byte through its

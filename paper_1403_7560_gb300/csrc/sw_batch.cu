@@ -181,6 +181,10 @@ int sw_batch_add(sw_batch* b, sw_handle* h) {
     return bfail(SW_ERR_BAD_ARG, "batches hold Ising and Potts lattices only");
   if (h->dim != b->dim) return bfail(SW_ERR_BAD_ARG, "lattice dimension differs from the batch's");
   if (h->batch) return bfail(SW_ERR_BAD_ARG, "lattice already belongs to a batch");
+  // the batch stream does not wait for the lattice's own stream or uploads
+  cudaError_t e = swgb::wait_io(h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bcuda(e, "lattice sync");
   b->members.push_back(h);
   h->batch = b;
   b->dirty = true;

@@ -107,6 +107,7 @@ int draw_bits(int model, int q) {
 
 void release(sw_handle* h) {
   if (!h) return;
+  swgb::release_io(h);
   cudaFree(h->lat.spins);
   cudaFree(h->lat.planes);
   cudaFree(h->lat.forest);
@@ -362,6 +363,8 @@ int sw_discard(sw_handle* h, int n) { return run_sweeps(h, n, false); }
 
 int sw_sync(sw_handle* h) {
   if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  const cudaError_t e = swgb::wait_io(h);
+  if (e != cudaSuccess) return cuda_fail(e, "asynchronous I/O");
   return check_device_error(h);
 }
 

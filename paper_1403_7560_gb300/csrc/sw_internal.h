@@ -150,6 +150,10 @@ cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cud
 cudaError_t flush_pending(struct ::sw_handle* h);
 // Bytes of the small per-handle buffers (records, sums, accumulators).
 size_t handle_block_bytes();
+// Waits for the handle's asynchronous uploads and downloads (no-op if none).
+cudaError_t wait_io(sw_handle* h);
+// Frees the asynchronous I/O streams, events and buffers.
+void release_io(sw_handle* h);
 
 }  // namespace swgb
 
@@ -170,4 +174,12 @@ struct sw_handle {
   void* d_block = nullptr;      // one allocation holding every small buffer
   void* d_clock = nullptr;      // clock model: thresholds, cos/sin, histograms
   struct sw_batch* batch = nullptr;  // batch the lattice belongs to, if any
+  // asynchronous host I/O (sw_io.cu), created on first use: an upload and a
+  // download stream, the upload target (swapped with lat.spins when the
+  // upload is installed) and the download snapshot, with their events
+  cudaStream_t io_in = nullptr, io_out = nullptr;
+  void* stage_in = nullptr;
+  void* snap = nullptr;
+  cudaEvent_t ev_in_done = nullptr, ev_in_free = nullptr, ev_snap = nullptr, ev_out_done = nullptr;
+  bool in_free_set = false, out_done_set = false;
 };

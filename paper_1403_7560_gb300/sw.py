@@ -63,6 +63,10 @@ _SIGNATURES = {
     "sw_get_bonds": (_i, [_vp, _vp, _sz]),
     "sw_label_from_bonds": (_i, [_vp, _vp, _vp]),
     "sw_relabel": (_i, [_vp, _i, _vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i)]),
+    "sw_set_spins_async": (_i, [_vp, _vp, _sz]),
+    "sw_get_spins_async": (_i, [_vp, _vp, _sz]),
+    "sw_get_record_async": (_i, [_vp, _u64, ctypes.POINTER(sw_record)]),
+    "sw_wait_io": (_i, [_vp]),
     "sw_get_series": (_i, [_vp, _u64, _sz, ctypes.POINTER(sw_record)]),
     "sw_series_capacity": (_sz, []),
     "sw_sweep_timed": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i]),
@@ -232,6 +236,42 @@ def sw_relabel(h: Handle, method: int, want_labels: bool = True):
     _check(lib().sw_relabel(h, method, out.ctypes.data if want_labels else None,
                             ctypes.byref(ms), ctypes.byref(it)))
     return out, float(ms.value), int(it.value)
+
+
+def sw_set_spins_async(h: Handle, host: np.ndarray):
+    """Enqueue the upload of `host` (a page-locked array, e.g. a numpy view
+    of a pinned torch tensor, kept unchanged until sw_wait_io)."""
+    _check(lib().sw_set_spins_async(h, host.ctypes.data, host.nbytes))
+
+
+def sw_get_spins_async(h: Handle, host: np.ndarray):
+    """Enqueue the download of the state into the page-locked array `host`
+    (valid after sw_wait_io)."""
+    _check(lib().sw_get_spins_async(h, host.ctypes.data, host.nbytes))
+
+
+def sw_get_record_async(h: Handle, sweep: int, rec) -> None:
+    """Enqueue the download of one sweep record into `rec`, a sw_record in
+    page-locked memory (see record_buffer); valid after sw_wait_io."""
+    _check(lib().sw_get_record_async(h, sweep, ctypes.byref(rec)))
+
+
+def sw_wait_io(h: Handle):
+    _check(lib().sw_wait_io(h))
+
+
+def record_buffer(n: int):
+    """n sw_record structs in page-locked host memory (kept alive by the
+    returned object's `owner`)."""
+    import torch
+    t = torch.empty(n * ctypes.sizeof(sw_record), dtype=torch.uint8, pin_memory=True)
+    arr = (sw_record * n).from_address(t.data_ptr())
+    arr.owner = t
+    return arr
+
+
+def record_dict(rec) -> dict:
+    return {f: getattr(rec, f) for f, _ in sw_record._fields_}
 
 
 def sw_get_series(h: Handle, first: int, count: int) -> list[dict]:

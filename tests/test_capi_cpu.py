@@ -66,6 +66,10 @@ def test_null_handle_calls_fail_cleanly(swlib):
     assert lib.sw_sync(None) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_num_sites(None) == 0
     assert lib.sw_relabel(None, swlib.SW_LABEL_EQUIVALENCE, None, None, None) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_set_spins_async(None, None, 0) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_get_spins_async(None, None, 0) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_get_record_async(None, 1, None) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_wait_io(None) == swlib.SW_ERR_BAD_ARG
     lib.sw_destroy(None)
     assert swlib.sw_series_capacity() >= 1024
 
