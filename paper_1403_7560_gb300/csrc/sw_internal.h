@@ -154,6 +154,8 @@ size_t handle_block_bytes();
 cudaError_t wait_io(sw_handle* h);
 // Frees the asynchronous I/O streams, events and buffers.
 void release_io(sw_handle* h);
+// Device-side copy of `bytes` by a kernel (buffers from cudaMalloc).
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 }  // namespace swgb
 
@@ -181,5 +183,6 @@ struct sw_handle {
   void* stage_in = nullptr;
   void* snap = nullptr;
   cudaEvent_t ev_in_done = nullptr, ev_in_free = nullptr, ev_snap = nullptr, ev_out_done = nullptr;
+  cudaEvent_t ev_rec = nullptr;
   bool in_free_set = false, out_done_set = false;
 };

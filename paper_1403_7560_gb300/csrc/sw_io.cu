@@ -5,16 +5,22 @@
 // off the sweep's critical path.  Uploads run on their own stream into a
 // staging buffer that is swapped with the state buffer once the upload is
 // done (kernels launched afterwards read the new state); downloads copy the
-// state into a snapshot buffer on the compute stream (a device-to-device
-// copy) and from there to the host on a second stream, so the next sweep
+// state into a snapshot buffer on the compute stream (a copy kernel) and
+// from there to the host on a second stream, so the next sweep
 // may overwrite the state while the download runs.  Events order the three
 // streams:
 //   upload k:   io_in waits ev_in_free (the buffer it fills is no longer
 //               read), copies, records ev_in_done; the compute stream waits
 //               ev_in_done, the buffers are swapped, ev_in_free is recorded.
 //   download k: the compute stream waits ev_out_done (the snapshot is no
-//               longer read), copies the state to the snapshot, records
-//               ev_snap; io_out waits ev_snap, copies, records ev_out_done.
+//               longer read), copies the state to the snapshot with a copy
+//               kernel (so no copy engine is shared with the downloads),
+//               records ev_snap; io_out waits ev_snap, copies, records
+//               ev_out_done.
+//   record:     the compute stream records ev_rec once the record is final;
+//               io_out waits ev_rec and copies it (small copies issued on
+//               the compute stream would queue behind a download on the
+//               same copy engine and stall the sweeps).
 #include <string>
 #include <utility>
 
@@ -22,6 +28,15 @@
 #include "sw_internal.h"
 
 namespace {
+
+// 16-byte words, then the remaining bytes (buffers from cudaMalloc, so both
+// start 256-byte aligned).
+__global__ void __launch_bounds__(256) k_copy(uint4* dst, const uint4* src, size_t n16, uint8_t* dst1,
+                                              const uint8_t* src1, size_t n1) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = __ldcs(&src[i]);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride) dst1[i] = src1[i];
+}
 
 int io_fail(int code, const std::string& msg) {
   swgb::set_last_error(msg);
@@ -38,7 +53,7 @@ cudaError_t ensure_io(sw_handle* h) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, h->spin_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->snap, h->spin_bytes);
-  cudaEvent_t* evs[4] = {&h->ev_in_done, &h->ev_in_free, &h->ev_snap, &h->ev_out_done};
+  cudaEvent_t* evs[5] = {&h->ev_in_done, &h->ev_in_free, &h->ev_snap, &h->ev_out_done, &h->ev_rec};
   for (cudaEvent_t* ev : evs)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -57,6 +72,17 @@ int check_io_args(sw_handle* h, const void* host, size_t bytes) {
 
 }  // namespace
 
+cudaError_t swgb::launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  const size_t n16 = bytes / 16, tail = bytes % 16;
+  size_t g = (n16 + 255) / 256;
+  if (g > 152u * 8u) g = 152u * 8u;
+  if (g == 0) g = 1;
+  k_copy<<<(unsigned)g, 256, 0, st>>>(static_cast<uint4*>(dst), static_cast<const uint4*>(src), n16,
+                                      static_cast<uint8_t*>(dst) + 16 * n16,
+                                      static_cast<const uint8_t*>(src) + 16 * n16, tail);
+  return cudaGetLastError();
+}
+
 cudaError_t swgb::wait_io(sw_handle* h) {
   cudaError_t e = cudaSuccess;
   if (h->io_in) e = cudaStreamSynchronize(h->io_in);
@@ -67,10 +93,10 @@ cudaError_t swgb::wait_io(sw_handle* h) {
 void swgb::release_io(sw_handle* h) {
   if (h->io_in) cudaStreamSynchronize(h->io_in);
   if (h->io_out) cudaStreamSynchronize(h->io_out);
-  cudaEvent_t evs[4] = {h->ev_in_done, h->ev_in_free, h->ev_snap, h->ev_out_done};
+  cudaEvent_t evs[5] = {h->ev_in_done, h->ev_in_free, h->ev_snap, h->ev_out_done, h->ev_rec};
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
-  h->ev_in_done = h->ev_in_free = h->ev_snap = h->ev_out_done = nullptr;
+  h->ev_in_done = h->ev_in_free = h->ev_snap = h->ev_out_done = h->ev_rec = nullptr;
   cudaFree(h->stage_in);
   cudaFree(h->snap);
   h->stage_in = h->snap = nullptr;
@@ -107,7 +133,7 @@ int sw_get_spins_async(sw_handle* h, void* host, size_t bytes) {
   cudaError_t e = ensure_io(h);
   if (e != cudaSuccess) return io_cuda(e, "asynchronous I/O setup");
   if (h->out_done_set) e = cudaStreamWaitEvent(h->stream, h->ev_out_done, 0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->snap, h->lat.spins, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = swgb::launch_copy(h->snap, h->lat.spins, bytes, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_snap, h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_snap, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, h->snap, bytes, cudaMemcpyDeviceToHost, h->io_out);
@@ -122,13 +148,16 @@ int sw_get_record_async(sw_handle* h, uint64_t sweep, sw_record* host) {
   if (sweep == 0 || sweep > h->sweep) return io_fail(SW_ERR_RANGE, "sweep not run yet");
   if (h->sweep - sweep >= (uint64_t)h->meas.series_cap)
     return io_fail(SW_ERR_RANGE, "sweep record no longer retained");
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = ensure_io(h);
+  if (e != cudaSuccess) return io_cuda(e, "asynchronous I/O setup");
   if (h->pending == sweep) e = swgb::flush_pending(h);
   static_assert(sizeof(swgb::Record) == sizeof(sw_record), "record layout");
   const swgb::Record* ring = static_cast<const swgb::Record*>(h->meas.series);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_rec, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_rec, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(host, ring + (sweep % (uint64_t)h->meas.series_cap), sizeof(sw_record),
-                        cudaMemcpyDeviceToHost, h->stream);
+                        cudaMemcpyDeviceToHost, h->io_out);
   return e == cudaSuccess ? SW_OK : io_cuda(e, "get_record_async");
 }
 
