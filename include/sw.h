@@ -45,9 +45,11 @@
  *     word d of counter (i, sweep, 1, 0) and t[a][b] = floor(-expm1(-(2/T)
  *     x_a x_b) 2^32) where x_a x_b > 0, else 0 (double, computed once per
  *     lattice).  Clusters reflect when their root's draw w >= 2^31.  Moments
- *     come from integer histograms of states and of bond differences
- *     (p_i - p_j) mod q summed against cos/sin((2 pi k)/q) in index order,
- *     so trajectories and moments are reproducible bit for bit.
+ *     are exact integer sums of the fixed-point tables C[k] = round(2^30
+ *     cos(2 pi k / q)) and S[k] = round(2^30 sin(2 pi k / q)): mx = 2^-30
+ *     sum_i C[p_i], my = 2^-30 sum_i S[p_i], E = -2^-30 sum_<ij>
+ *     C[(p_i - p_j) mod q], each integer sum converted to double once, so
+ *     trajectories and moments are reproducible bit for bit.
  *   - Ownership: the handle owns every device buffer it allocates; host
  *     buffers passed in stay owned by the caller and are only read or
  *     written during the call (the call synchronises the handle's stream).

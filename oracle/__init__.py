@@ -99,6 +99,8 @@ def lib():
             dp = ctypes.POINTER(ctypes.c_double)
             L.oracle_clock_trig.argtypes = [ctypes.c_int, dp, dp]
             L.oracle_clock_thresholds.argtypes = [ctypes.c_int, ctypes.c_double, u32p]
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            L.oracle_clock_fixed.argtypes = [ctypes.c_int, i64p, i64p]
             L.oracle_clock_mirror.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int]
             L.oracle_clock_mirror.restype = ctypes.c_uint32
             _lib = L
@@ -149,6 +151,15 @@ def clock_trig(q: int):
     s = np.zeros(q, dtype=np.float64)
     lib().oracle_clock_trig(q, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                             s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return c, s
+
+
+def clock_fixed(q: int):
+    """Fixed-point tables round(2^30 cos(2 pi p / q)), round(2^30 sin(...))."""
+    c = np.zeros(q, dtype=np.int64)
+    s = np.zeros(q, dtype=np.int64)
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    lib().oracle_clock_fixed(q, c.ctypes.data_as(p64), s.ctypes.data_as(p64))
     return c, s
 
 

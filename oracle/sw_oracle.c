@@ -54,9 +54,12 @@
  * mod q (the mirror line at angle pi s / q); the Ising projection of site i
  * is x_i = sin(pi k_i / q) with k_i = (2 p_i - s) mod 2q.  Bond (i,d) is
  * active iff x_i x_j > 0 and u(i,d) < t[k_i][k_j], t = floor((1 - exp(-2K
- * x_a x_b)) 2^32) from a table evaluated in double.  Moments come from the
- * integer histograms of states and of bond differences (p_i - p_j) mod q,
- * summed against cos/sin tables in index order.
+ * x_a x_b)) 2^32) from a table evaluated in double.  Moments are exact
+ * integer sums of fixed-point tables C[k] = round(2^30 cos(2 pi k / q)),
+ * S[k] = round(2^30 sin(2 pi k / q)): mx = 2^-30 sum_i C[p_i], my likewise
+ * with S, and E = -2^-30 sum_<ij> C[(p_i - p_j) mod q]; each integer sum is
+ * converted to double once, so the result does not depend on the order of
+ * the sites.
  */
 #include <math.h>
 #include <stdint.h>
@@ -185,6 +188,16 @@ void oracle_clock_trig(int q, double* cosv, double* sinv) {
     const double a = (2.0 * OR_PI * (double)p) / (double)q;
     cosv[p] = cos(a);
     sinv[p] = sin(a);
+  }
+}
+
+/* Fixed-point clock tables: C[p] = round(2^30 cos(2 pi p / q)), S[p] =
+ * round(2^30 sin(2 pi p / q)) (nearest, halves away from zero). */
+void oracle_clock_fixed(int q, int64_t* C, int64_t* S) {
+  for (int p = 0; p < q; ++p) {
+    const double a = (2.0 * OR_PI * (double)p) / (double)q;
+    C[p] = llround(ldexp(cos(a), 30));
+    S[p] = llround(ldexp(sin(a), 30));
   }
 }
 
@@ -479,22 +492,18 @@ void oracle_moments(int model, int dim, int L, int q, const void* spins,
     rec->Ed = (double)E;
   } else if (model == OR_CLOCK) {
     const uint16_t* s = (const uint16_t*)spins;
-    int64_t* n = (int64_t*)calloc((size_t)q, sizeof(int64_t));
-    int64_t* b = (int64_t*)calloc((size_t)q, sizeof(int64_t));
-    double* c = (double*)malloc(sizeof(double) * (size_t)q);
-    double* sn = (double*)malloc(sizeof(double) * (size_t)q);
-    oracle_clock_trig(q, c, sn);
+    int64_t* C = (int64_t*)malloc(sizeof(int64_t) * (size_t)q);
+    int64_t* S = (int64_t*)malloc(sizeof(int64_t) * (size_t)q);
+    oracle_clock_fixed(q, C, S);
+    int64_t mxi = 0, myi = 0, eb = 0;
     for (int64_t i = 0; i < N; ++i) {
-      n[s[i]] += 1;
-      for (int d = 0; d < dim; ++d) b[((int)s[i] - (int)s[neighbour(dim, L, i, d)] + q) % q] += 1;
+      mxi += C[s[i]];
+      myi += S[s[i]];
+      for (int d = 0; d < dim; ++d) eb += C[((int)s[i] - (int)s[neighbour(dim, L, i, d)] + q) % q];
     }
-    double mx = 0.0, my = 0.0, e = 0.0;
-    for (int k = 0; k < q; ++k) {
-      mx += (double)n[k] * c[k];
-      my += (double)n[k] * sn[k];
-      e -= (double)b[k] * c[k];
-    }
-    free(n); free(b); free(c); free(sn);
+    free(C); free(S);
+    const double mx = (double)mxi * 0x1p-30, my = (double)myi * 0x1p-30;
+    const double e = -((double)eb * 0x1p-30);
     rec->mx = mx;
     rec->my = my;
     rec->e_xy = e;

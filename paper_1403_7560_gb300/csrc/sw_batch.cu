@@ -268,7 +268,7 @@ size_t sw_device_bytes(int model, int dim, int L, int q) {
   const size_t words = (size_t)dim * (N / (size_t)L) * (size_t)((L + 31) / 32);
   const size_t ntiles = (size_t)ntx * nty * ntz;
   const size_t spins = N * (model == SW_XY ? 4 : model == SW_CLOCK ? 2 : 1);
-  const size_t clock = (model == SW_CLOCK) ? (size_t)4 * q * q * 4 + (size_t)2 * q * 16 : 0;
+  const size_t clock = (model == SW_CLOCK) ? (size_t)4 * q * q * 4 + (size_t)2 * q * 8 + 3 * swgb::kSlots * 8 : 0;
   return spins + 4 * words + 4 * N + ntiles * (size_t)swgb::merge_list_capacity(dim) * 4 + ntiles * 4 +
          swgb::handle_block_bytes() + clock;
 }

@@ -70,12 +70,13 @@ uint32_t bond_threshold(int model, double T) {
   return (uint32_t)t;
 }
 
-// Clock model tables, per the definition in include/sw.h: cos/sin of
-// (2 pi p)/q, and thresholds floor(-expm1(-(2/T) x_a x_b) 2^32) with
-// x_k = sin((pi k)/q), zero where x_a x_b <= 0.
+// Clock model tables, per the definition in include/sw.h: fixed-point
+// round(2^30 cos/sin((2 pi p)/q)), and thresholds
+// floor(-expm1(-(2/T) x_a x_b) 2^32) with x_k = sin((pi k)/q), zero where
+// x_a x_b <= 0.
 constexpr double kPi = 3.141592653589793238463;
 
-void clock_tables(int q, double T, std::vector<uint32_t>& tab, std::vector<double>& trig) {
+void clock_tables(int q, double T, std::vector<uint32_t>& tab, std::vector<long long>& fix) {
   const int q2 = 2 * q;
   std::vector<double> x(q2);
   for (int k = 0; k < q2; ++k) x[k] = std::sin((kPi * (double)k) / (double)q);
@@ -90,11 +91,11 @@ void clock_tables(int q, double T, std::vector<uint32_t>& tab, std::vector<doubl
         tab[(size_t)a * q2 + b] = (uint32_t)f;
       }
     }
-  trig.assign(q2, 0.0);
+  fix.assign(q2, 0);
   for (int p = 0; p < q; ++p) {
     const double ang = (2.0 * kPi * (double)p) / (double)q;
-    trig[p] = std::cos(ang);
-    trig[q + p] = std::sin(ang);
+    fix[p] = std::llround(std::ldexp(std::cos(ang), 30));
+    fix[q + p] = std::llround(std::ldexp(std::sin(ang), 30));
   }
 }
 
@@ -135,7 +136,7 @@ int check_device_error(sw_handle* h) {
 // Step (1) and the tile half of step (2): Ising/Potts bonds are drawn inside
 // the labeling kernel, which also measures the incoming state when the
 // previous sweep's record is pending; XY and clock bonds come from their own
-// kernel (the XY one measures the pending state too).  Sets *finalize to
+// kernels, which measure the pending state the same way.  Sets *finalize to
 // the pending sweep whose record the flip kernel of this sweep must write
 // (0 if none).
 cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k, uint32_t* finalize) {
@@ -153,7 +154,13 @@ cudaError_t launch_bonds_labels(sw_handle* h, uint32_t k, uint32_t* finalize) {
       e = swgb::launch_bonds_xy(h->lat, k, m, &blocks, h->stream);
       if (m) h->meas.xy_blocks = blocks;
     } else {
-      e = swgb::launch_bonds_clock(h->lat, k, h->stream);
+      const swgb::Measure* m = nullptr;
+      if (h->pending) {
+        *finalize = (uint32_t)h->pending;
+        h->pending = 0;
+        m = &h->meas;
+      }
+      e = swgb::launch_bonds_clock(h->lat, k, m, h->stream);
     }
     if (e != cudaSuccess) return e;
     return swgb::launch_label(h->lat, k, true, h->stream);
@@ -181,9 +188,8 @@ cudaError_t swgb::flush_pending(sw_handle* h) {
 namespace {
 using swgb::flush_pending;
 
-// One sweep; Ising/Potts/XY leave their measurement pending (it is taken
-// from the next sweep's bond kernel or by flush_pending), clock measures at
-// once.
+// One sweep; the measurement stays pending (it is taken from the next
+// sweep's bond kernel, or by flush_pending).
 cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   cudaError_t e = cudaSuccess;
   uint32_t finalize = 0u;
@@ -195,8 +201,7 @@ cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas, measure, finalize, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->stream);
   if (e == cudaSuccess && measure) {
-    if (h->model == SW_CLOCK) e = swgb::launch_measure(h->lat, h->model, k, h->meas, h->stream);
-    else h->pending = k;
+    h->pending = k;
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], h->stream);
   return e;
@@ -292,11 +297,12 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   h->meas.series_cap = kSeriesCap;
 
   if (model == SW_CLOCK) {
-    // clock tables (thresholds, cos/sin) and histograms in one allocation
+    // clock tables (thresholds, fixed-point cos/sin) and slot sums in one allocation
     std::vector<uint32_t> tab;
-    std::vector<double> trig;
+    std::vector<long long> trig;
     clock_tables(q, T, tab, trig);
-    const size_t tab_bytes = tab.size() * 4, trig_bytes = trig.size() * 8, hist_bytes = (size_t)2 * q * 8;
+    const size_t tab_bytes = tab.size() * 4, trig_bytes = trig.size() * 8;
+    const size_t hist_bytes = (size_t)3 * swgb::kSlots * 8;
     if ((e = cudaMalloc(&h->d_clock, tab_bytes + trig_bytes + hist_bytes)) != cudaSuccess) {
       fail(SW_ERR_OOM, std::string("clock tables: ") + cudaGetErrorString(e));
       cudaGetLastError();
@@ -305,8 +311,8 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
     }
     char* c = static_cast<char*>(h->d_clock);
     lat.ctab = reinterpret_cast<const uint32_t*>(c);
-    h->meas.ctrig = reinterpret_cast<const double*>(c + tab_bytes);
-    h->meas.chist = reinterpret_cast<unsigned long long*>(c + tab_bytes + trig_bytes);
+    h->meas.cfix = reinterpret_cast<const long long*>(c + tab_bytes);
+    h->meas.csums = reinterpret_cast<unsigned long long*>(c + tab_bytes + trig_bytes);
     if ((e = cudaMemcpy(c, tab.data(), tab_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c + tab_bytes, trig.data(), trig_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(c + tab_bytes + trig_bytes, 0, hist_bytes)) != cudaSuccess) {

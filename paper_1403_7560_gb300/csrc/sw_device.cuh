@@ -294,6 +294,22 @@ __device__ __forceinline__ void add_integer_sums(const Measure& mb, uint32_t slo
   }
 }
 
+// Add a block's clock sums (fixed-point cos, sin of the states and cos of
+// the bond differences) into its slot.
+template <int NW>
+__device__ __forceinline__ void add_clock_sums(const Measure& mb, uint32_t slot_of, long long cx,
+                                               long long sy, long long eb, long long* s_red) {
+  const long long X = block_combine<NW>(warp_sum(cx), s_red);
+  const long long Y = block_combine<NW>(warp_sum(sy), s_red);
+  const long long B = block_combine<NW>(warp_sum(eb), s_red);
+  if (threadIdx.x == 0) {
+    unsigned long long* slot = mb.csums + 3 * (slot_of % kSlots);
+    if (X) atomicAdd(&slot[0], (unsigned long long)X);
+    if (Y) atomicAdd(&slot[1], (unsigned long long)Y);
+    if (B) atomicAdd(&slot[2], (unsigned long long)B);
+  }
+}
+
 // Add a block's Potts histogram (shared bins) into its slot.
 __device__ __forceinline__ void add_histogram(const Lattice& lat, const Measure& mb, uint32_t slot_of,
                                               const unsigned int* s_hist) {
@@ -327,6 +343,23 @@ __device__ __forceinline__ void finalize_record(const Lattice& lat, const Measur
     mx = block_combine<NW>(warp_sum(a), s_rd);
     my = block_combine<NW>(warp_sum(c), s_rd);
     exy = block_combine<NW>(warp_sum(g), s_rd);
+  } else if (lat.model == kClock) {
+    // exact integer sums, converted to double once
+    long long a = 0, c = 0, g = 0;
+    for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {
+      a += (long long)__ldcg(&mb.csums[3 * k + 0]);
+      c += (long long)__ldcg(&mb.csums[3 * k + 1]);
+      g += (long long)__ldcg(&mb.csums[3 * k + 2]);
+      mb.csums[3 * k + 0] = 0ull;
+      mb.csums[3 * k + 1] = 0ull;
+      mb.csums[3 * k + 2] = 0ull;
+    }
+    const long long X = block_combine<NW>(warp_sum(a), s_ri);
+    const long long Y = block_combine<NW>(warp_sum(c), s_ri);
+    const long long B = block_combine<NW>(warp_sum(g), s_ri);
+    mx = __dmul_rn((double)X, 0x1p-30);
+    my = __dmul_rn((double)Y, 0x1p-30);
+    exy = -__dmul_rn((double)B, 0x1p-30);
   } else {
     long long a = 0, c = 0, g = 0;
     for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {

@@ -58,8 +58,8 @@ struct Measure {
   unsigned long long* sums;       // [kSlots][2]: integer M, E (two's complement)
   unsigned long long* hist;       // [kSlots][256]: Potts histogram
   double* part_d;                 // XY per-block partials [3 * kMeasureBlocks]
-  unsigned long long* chist;      // clock: histograms of states [q] and bond differences [q]
-  const double* ctrig;            // clock: cos(2 pi p / q) [q], sin [q]
+  unsigned long long* csums;      // clock: [kSlots][3] integer sums of C[p_i], S[p_i], C[p_i - p_j]
+  const long long* cfix;          // clock: C[p] = round(2^30 cos(2 pi p / q)) [q], then S [q]
   int xy_blocks;                  // blocks that wrote part_d
   double* acc;                    // n, sum M2, M4, E, E2, nclusters
   void* series;                   // sw_record ring
@@ -117,7 +117,9 @@ cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
 cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, const Measure* m, int* blocks,
                             cudaStream_t st);
 // Bonds of the clock model (lane per site, table thresholds).
-cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, cudaStream_t st);
+// Clock bonds of `sweep`; with m != nullptr the kernel also measures the
+// incoming state into m's clock slot sums.
+cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, const Measure* m, cudaStream_t st);
 // Tile labels (+ Ising/Potts bonds when from_mask is false; cluster draws
 // when sweep != 0) into the forest.
 cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st);
@@ -174,7 +176,7 @@ struct sw_handle {
   uint64_t pending = 0;         // measured sweep whose record is not yet written
   int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
   void* d_block = nullptr;      // one allocation holding every small buffer
-  void* d_clock = nullptr;      // clock model: thresholds, cos/sin, histograms
+  void* d_clock = nullptr;      // clock model: thresholds, fixed-point cos/sin, slot sums
   struct sw_batch* batch = nullptr;  // batch the lattice belongs to, if any
   // asynchronous host I/O (sw_io.cu), created on first use: an upload and a
   // download stream, the upload target (swapped with lat.spins when the

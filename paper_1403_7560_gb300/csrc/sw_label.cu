@@ -444,19 +444,25 @@ __global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattic
 // q-state clock: x_i = sin(pi k_i / q), k_i = (2 p_i - s) mod 2q for the
 // sweep's mirror index s; bond (i,d) active iff u(i,d) < t[k_i][k_j] (the
 // table is 0 where x_i x_j <= 0); u(i,d) = word d of Philox(i, sweep, BOND, 0).
-template <int D>
-__global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lattice lat, uint32_t sweep) {
+// With MEASURE the same loads measure the incoming state: integer sums of
+// the fixed-point tables C[p_i], S[p_i] and C[(p_i - p_j) mod q], added to
+// the clock slots per block.
+template <int D, bool MEASURE>
+__global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lattice lat, uint32_t sweep,
+                                                      const __grid_constant__ Measure mb) {
   __shared__ uint32_t s_mirror;
+  __shared__ long long s_red[256 / 32];
   if (threadIdx.x == 0) s_mirror = clock_mirror(lat, sweep);
   __syncthreads();
   const int L = lat.L, lane = threadIdx.x & 31;
-  const int q2 = 2 * lat.q;
+  const int q = lat.q, q2 = 2 * q;
   const int mirror = (int)s_mirror;
   const uint32_t nwords = lat.R * (uint32_t)lat.W;
   const uint32_t plane = nwords;
   const uint16_t* sp = static_cast<const uint16_t*>(lat.spins);
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  long long cx = 0, sy = 0, eb = 0;
   for (uint32_t g = gw; g < nwords; g += nw) {
     const uint32_t row = g / (uint32_t)lat.W, xw = g % (uint32_t)lat.W;
     const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
@@ -469,11 +475,18 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
       jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
       jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
       jn[2] = (D == 3) ? ((z + 1 == (uint32_t)L) ? i - z * L * L : i + (uint32_t)L * L) : 0u;
-      const int ki = ((2 * (int)sp[i] - mirror) % q2 + q2) % q2;
+      const int pi = sp[i];
+      const int ki = ((2 * pi - mirror) % q2 + q2) % q2;
+      if (MEASURE) {
+        cx += __ldg(&mb.cfix[pi]);
+        sy += __ldg(&mb.cfix[q + pi]);
+      }
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const int kj = ((2 * (int)sp[jn[d]] - mirror) % q2 + q2) % q2;
+        const int pj = sp[jn[d]];
+        const int kj = ((2 * pj - mirror) % q2 + q2) % q2;
         a |= (uint32_t)(word_of(w, d) < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj])) << d;
+        if (MEASURE) eb += __ldg(&mb.cfix[(pi - pj + q) % q]);
       }
     }
 #pragma unroll
@@ -482,16 +495,23 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
       if (lane == d) lat.planes[d * plane + g] = bal;
     }
   }
+  if (MEASURE) add_clock_sums<256 / 32>(mb, blockIdx.x, cx, sy, eb, s_red);
 }
 
 }  // namespace
 
-cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, cudaStream_t st) {
+cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, const Measure* m, cudaStream_t st) {
   const uint32_t words = lat.R * (uint32_t)lat.W;
   unsigned g = (words + 7u) / 8u;
   if (g > 4096u) g = 4096u;
-  if (lat.dim == 2) k_bonds_clock<2><<<g, 256, 0, st>>>(lat, sweep);
-  else k_bonds_clock<3><<<g, 256, 0, st>>>(lat, sweep);
+  const Measure none{};
+  if (lat.dim == 2) {
+    if (m) k_bonds_clock<2, true><<<g, 256, 0, st>>>(lat, sweep, *m);
+    else k_bonds_clock<2, false><<<g, 256, 0, st>>>(lat, sweep, none);
+  } else {
+    if (m) k_bonds_clock<3, true><<<g, 256, 0, st>>>(lat, sweep, *m);
+    else k_bonds_clock<3, false><<<g, 256, 0, st>>>(lat, sweep, none);
+  }
   return cudaGetLastError();
 }
 

@@ -3,8 +3,9 @@
 // Sec. 3: the moments entering U = <M^4>/<M^2>^2).
 //
 // k_measure: one warp per lattice row (grid-stride), lane per site;
-//   integer M / E / Potts histogram (warp-aggregated shared atomics) added
-//   to the measurement slots, or float XY per-block partials.
+//   integer M / E / Potts histogram (warp-aggregated shared atomics) or the
+//   clock model's fixed-point cos / sin sums added to the measurement
+//   slots, or float XY per-block partials.
 // k_finalize: one block sums slots / partials in a fixed order, writes the
 //   sweep record and adds M2, M2^2, E, E^2 and the cluster count to the FP64
 //   accumulators (explicit round-to-nearest operations, no contraction).
@@ -35,15 +36,15 @@ constexpr int kMThreads = 256, kMWarps = kMThreads / 32;
 
 template <int MODEL, int D>
 __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t sweep, Measure mb) {
-  __shared__ unsigned int s_hist[MODEL == kClock ? 2 * kMaxClockQ : 256];
+  __shared__ unsigned int s_hist[256];
   __shared__ long long s_ri[kMWarps];
   __shared__ double s_rd[kMWarps];
   const int L = lat.L, lane = threadIdx.x & 31;
-  if (MODEL == kPotts || MODEL == kClock) {
-    for (int k = threadIdx.x; k < (MODEL == kClock ? 2 * lat.q : lat.q); k += blockDim.x) s_hist[k] = 0u;
+  if (MODEL == kPotts) {
+    for (int k = threadIdx.x; k < lat.q; k += blockDim.x) s_hist[k] = 0u;
     __syncthreads();
   }
-  long long m = 0, e = 0;
+  long long m = 0, e = 0, cb = 0;
   float fx = 0.f, fy = 0.f, fe = 0.f;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -76,13 +77,14 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
         const unsigned grp = __match_any_sync(__activemask(), si);
         if (lane == __ffs(grp) - 1) atomicAdd(&s_hist[si], (unsigned)__popc(grp));
       } else if (MODEL == kClock) {
-        // histograms of states and of bond differences (p_i - p_j) mod q
+        // fixed-point sums: C[p_i], S[p_i] and C[(p_i - p_j) mod q]
         const uint16_t* sp = static_cast<const uint16_t*>(lat.spins);
         const int q = lat.q;
         const int pi = sp[i];
-        atomicAdd(&s_hist[pi], 1u);
+        m += __ldg(&mb.cfix[pi]);
+        e += __ldg(&mb.cfix[q + pi]);
 #pragma unroll
-        for (int d = 0; d < D; ++d) atomicAdd(&s_hist[q + (pi - (int)sp[jn[d]] + q) % q], 1u);
+        for (int d = 0; d < D; ++d) cb += __ldg(&mb.cfix[(pi - (int)sp[jn[d]] + q) % q]);
       } else {
         const float* th = static_cast<const float*>(lat.spins);
         const float ti = th[i];
@@ -100,9 +102,7 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
     add_histogram(lat, mb, blockIdx.x, s_hist);
   }
   if (MODEL == kClock) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < 2 * lat.q; k += blockDim.x)
-      if (s_hist[k]) atomicAdd(&mb.chist[k], (unsigned long long)s_hist[k]);
+    add_clock_sums<kMWarps>(mb, blockIdx.x, m, e, cb, s_ri);
     return;
   }
   if (MODEL != kXY) {
@@ -124,34 +124,7 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
 __global__ void __launch_bounds__(kMThreads) k_finalize(Lattice lat, uint32_t sweep, Measure mb) {
   __shared__ long long s_ri[kMWarps];
   __shared__ double s_rd[kMWarps];
-  __shared__ unsigned long long s_h[2 * kMaxClockQ];
-  __shared__ double s_m[3];
-  if (lat.model != kClock) {
-    finalize_record<kMWarps>(lat, mb, sweep, s_ri, s_rd);
-    return;
-  }
-  // clock: Mx = sum_p n_p cos_p, My = sum_p n_p sin_p, E = -sum_D b_D cos_D,
-  // in index order from the integer histograms
-  const int q = lat.q;
-  for (int k = threadIdx.x; k < 2 * q; k += blockDim.x) {
-    s_h[k] = __ldcg(&mb.chist[k]);
-    mb.chist[k] = 0ull;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mx = 0.0, my = 0.0, e = 0.0;
-    for (int k = 0; k < q; ++k) {
-      const double c = mb.ctrig[k], sn = mb.ctrig[q + k];
-      mx = __dadd_rn(mx, __dmul_rn((double)s_h[k], c));
-      my = __dadd_rn(my, __dmul_rn((double)s_h[k], sn));
-      e = __dsub_rn(e, __dmul_rn((double)s_h[q + k], c));
-    }
-    s_m[0] = mx;
-    s_m[1] = my;
-    s_m[2] = e;
-  }
-  __syncthreads();
-  commit_record<kMWarps>(lat, mb, sweep, 0, 0, 0, s_m[0], s_m[1], s_m[2], s_ri);
+  finalize_record<kMWarps>(lat, mb, sweep, s_ri, s_rd);
 }
 
 unsigned grid_for(uint32_t n_warps_work, unsigned cap) {

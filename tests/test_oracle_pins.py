@@ -364,6 +364,38 @@ def test_clock_512_approaches_xy():
         assert abs(mean[j] - ref[key]) < 4.5 * sig, (key, mean[j], ref[key], sig)
 
 
+@pytest.mark.parametrize("q", [2, 3, 4, 6, 512, 1024])
+def test_clock_fixed_point_tables(q):
+    c, s = oracle.clock_fixed(q)
+    a = 2 * np.pi * np.arange(q) / q
+    assert np.all(np.abs(c - np.cos(a) * 2.0 ** 30) <= 0.5 + 1e-6)
+    assert np.all(np.abs(s - np.sin(a) * 2.0 ** 30) <= 0.5 + 1e-6)
+    if q % 4 == 0:                                 # exact quarter turns
+        assert c[0] == 2 ** 30 and c[q // 4] == 0 and c[q // 2] == -2 ** 30 and s[q // 4] == 2 ** 30
+
+
+@pytest.mark.parametrize("dim,L,q", [(2, 17, 512), (3, 6, 5), (2, 8, 4)])
+def test_clock_moments_are_fixed_point_sums(dim, L, q):
+    """mx, my, E of a random clock state from integer sums of the rounded
+    tables, recomputed here with numpy's own trig (and, for q = 4, the exact
+    integer values)."""
+    p = inputs.random_spins(CLOCK, L ** dim, q, seed=q + L).astype(np.int64)
+    a = 2 * np.pi * np.arange(q) / q
+    C = np.rint(np.cos(a) * 2.0 ** 30).astype(np.int64)
+    S = np.rint(np.sin(a) * 2.0 ** 30).astype(np.int64)
+    eb = sum(int(C[(p - p[exact.neighbours(dim, L, d)]) % q].sum()) for d in range(dim))
+    rec = oracle.moments(CLOCK, dim, L, q, p.astype(np.uint16))
+    assert rec["mx"] == float(int(C[p].sum())) * 2.0 ** -30
+    assert rec["my"] == float(int(S[p].sum())) * 2.0 ** -30
+    assert rec["e_xy"] == -(float(eb) * 2.0 ** -30)
+    assert rec["M2"] == rec["mx"] * rec["mx"] + rec["my"] * rec["my"]
+    # against the plain floating definition
+    th = a[p]
+    assert abs(rec["mx"] - np.cos(th).sum()) < 1e-6 * p.size
+    e = -sum(np.cos(th - th[exact.neighbours(dim, L, d)]).sum() for d in range(dim))
+    assert abs(rec["e_xy"] - e) < 1e-6 * p.size * dim
+
+
 def test_clock_bonds_and_reflection():
     dim, L, q, T, seed = 2, 48, 64, 0.8, 3
     s = inputs.random_spins(CLOCK, L * L, q, seed=4)
