@@ -96,8 +96,6 @@ def lib():
             L.oracle_set_sweep_counter.argtypes = [vp, ctypes.c_uint32]
             L.oracle_last_record.argtypes = [vp, ctypes.POINTER(Record)]
             L.oracle_take_acc.argtypes = [vp, ctypes.POINTER(Acc)]
-            dp = ctypes.POINTER(ctypes.c_double)
-            L.oracle_clock_trig.argtypes = [ctypes.c_int, dp, dp]
             L.oracle_clock_thresholds.argtypes = [ctypes.c_int, ctypes.c_double, u32p]
             i64p = ctypes.POINTER(ctypes.c_int64)
             L.oracle_clock_fixed.argtypes = [ctypes.c_int, i64p, i64p]
@@ -144,14 +142,6 @@ def bond_threshold(model: int, T: float) -> int:
 
 def xy_phi(seed: int, sweep: int) -> np.float32:
     return np.float32(lib().oracle_xy_phi(seed, sweep))
-
-
-def clock_trig(q: int):
-    c = np.zeros(q, dtype=np.float64)
-    s = np.zeros(q, dtype=np.float64)
-    lib().oracle_clock_trig(q, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                            s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-    return c, s
 
 
 def clock_fixed(q: int):

@@ -178,18 +178,10 @@ float oracle_xy_phi(uint64_t seed, uint32_t sweep) {
 
 /* ------------------------------------------------------------------------ */
 /* Clock model tables.  Angle of state p: (2 pi p) / q in double; the
- * projection table x(k) = sin((pi k) / q) for k in [0, 2q); the threshold
+ * fixed-point cos/sin tables of the moments; the projection table x(k) = sin((pi k) / q) for k in [0, 2q); the threshold
  * table t[a][b] = floor(-expm1(-(2/T) x(a) x(b)) 2^32) where x(a) x(b) > 0,
  * else 0. */
 static const double OR_PI = 3.141592653589793238463;
-
-void oracle_clock_trig(int q, double* cosv, double* sinv) {
-  for (int p = 0; p < q; ++p) {
-    const double a = (2.0 * OR_PI * (double)p) / (double)q;
-    cosv[p] = cos(a);
-    sinv[p] = sin(a);
-  }
-}
 
 /* Fixed-point clock tables: C[p] = round(2^30 cos(2 pi p / q)), S[p] =
  * round(2^30 sin(2 pi p / q)) (nearest, halves away from zero). */

@@ -92,8 +92,8 @@ struct Record {
   double mx, my, e_xy, M2, Ed;
 };
 
-constexpr int kMeasureBlocks = 1216;
-constexpr int kMaxClockQ = 1024;  // largest q of the clock model  // 152 SMs x 8 blocks of 256 threads
+constexpr int kMeasureBlocks = 1216;  // 152 SMs x 8 blocks of 256 threads
+constexpr int kMaxClockQ = 1024;      // largest q of the clock model
 
 // Tile shape of the labeling, merge and flip kernels: 32 sites along x (one
 // bit-plane word) by TY (by TZ); one CTA of TY*TZ threads per tile.
