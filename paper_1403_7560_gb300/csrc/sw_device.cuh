@@ -107,6 +107,11 @@ __device__ __forceinline__ uint32_t eq_bits(const uint32_t* a, const uint32_t* b
   return m;
 }
 
+// v mod m for v in (-m, 2m), without a division.
+__device__ __forceinline__ int wrap_mod(int v, int m) {
+  return v < 0 ? v + m : (v >= m ? v - m : v);
+}
+
 // Highest set bit of `starts` at or below bit b (the start of b's x-run).
 __device__ __forceinline__ uint32_t run_start(uint32_t starts, int b) {
   return 31u - __clz(starts & (kFull >> (31 - b)));

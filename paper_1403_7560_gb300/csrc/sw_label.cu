@@ -407,9 +407,14 @@ __global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattic
           const float prod = __fmul_rn(si.x, sj.x);
           bool act = false;
           if (prod > 0.0f) {
-            const float p = -expm1f(-__fmul_rn(lat.twoK, prod));
+            // u < p with p = -expm1f(-2K prod): a fast estimate of p decides
+            // unless u lies within a margin far above the estimate's error
+            // (|a| <= 2K keeps __expf within a few ulp), where expm1f decides
+            const float a2 = __fmul_rn(lat.twoK, prod);
             const float u = __fmul_rn((float)(word_of(w, d) >> 8), 0x1p-24f);
-            act = u < p;
+            const float pf = __fsub_rn(1.0f, __expf(-a2));
+            if (fabsf(__fsub_rn(u, pf)) > 0x1p-16f) act = u < pf;
+            else act = u < -expm1f(-a2);
           }
           a |= (uint32_t)act << d;
           if (MEASURE) fe = __fadd_rn(fe, __fadd_rn(prod, __fmul_rn(si.y, sj.y)));
@@ -476,7 +481,7 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
       jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
       jn[2] = (D == 3) ? ((z + 1 == (uint32_t)L) ? i - z * L * L : i + (uint32_t)L * L) : 0u;
       const int pi = sp[i];
-      const int ki = ((2 * pi - mirror) % q2 + q2) % q2;
+      const int ki = wrap_mod(2 * pi - mirror, q2);
       if (MEASURE) {
         cx += __ldg(&mb.cfix[pi]);
         sy += __ldg(&mb.cfix[q + pi]);
@@ -484,9 +489,9 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const int pj = sp[jn[d]];
-        const int kj = ((2 * pj - mirror) % q2 + q2) % q2;
+        const int kj = wrap_mod(2 * pj - mirror, q2);
         a |= (uint32_t)(word_of(w, d) < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj])) << d;
-        if (MEASURE) eb += __ldg(&mb.cfix[(pi - pj + q) % q]);
+        if (MEASURE) eb += __ldg(&mb.cfix[wrap_mod(pi - pj, q)]);
       }
     }
 #pragma unroll

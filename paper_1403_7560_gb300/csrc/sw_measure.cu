@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
         m += __ldg(&mb.cfix[pi]);
         e += __ldg(&mb.cfix[q + pi]);
 #pragma unroll
-        for (int d = 0; d < D; ++d) cb += __ldg(&mb.cfix[(pi - (int)sp[jn[d]] + q) % q]);
+        for (int d = 0; d < D; ++d) cb += __ldg(&mb.cfix[wrap_mod(pi - (int)sp[jn[d]], q)]);
       } else {
         const float* th = static_cast<const float*>(lat.spins);
         const float ti = th[i];
