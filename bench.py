@@ -56,7 +56,7 @@ PHASES = ["bond_label", "merge", "flip", "measure"]
 # DRAM bytes (read + write) of one launch of the dominant kernel, k_label
 # with measurement, from one ncu capture of this build (cold cache; see
 # profiles/sweep_kernels_ising3d_L256.md); None once that kernel changes.
-KERNEL_DRAM_BYTES = {"bond_label": 16.851968e6 + 14.457088e6}
+KERNEL_DRAM_BYTES = {"bond_label": 16.864000e6 + 12.871680e6}
 # kernels one measured sweep launches: k_label (bonds + tile labels + the
 # previous sweep's measurement), k_merge, k_compress, k_apply
 KERNELS_PER_SWEEP = 4
@@ -382,7 +382,7 @@ def run_gpu(args):
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": KERNEL_DRAM_BYTES.get(PHASES[dom]),
                          "peak_source": f"{peak_kind} hbm_gbs",
-                         "limiter": "instruction issue (ncu: 69% issue active, 5.3 warp instr/site)",
+                         "limiter": "instruction issue (ncu: 68% issue active, 5.0 warp instr/site)",
                          "bytes_per_site": bps},
             "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
             "update_only": {"value": update_only, "unit": UNIT},
