@@ -89,6 +89,16 @@ def test_potts_sweeps_bit_exact(sw, dim, L, q, T):
     run_exact_parity(sw, POTTS, dim, L, q, T, seed=2000 + L, sweeps=12)
 
 
+@pytest.mark.parametrize("model,L,q,T,sweeps", [
+    (ISING, 60, 2, 4.5115, 10), (ISING, 64, 2, 3.9, 10), (ISING, 64, 2, 6.0, 6),
+    (ISING, 128, 2, 4.5115, 4), (POTTS, 62, 3, 1.8, 8), (POTTS, 64, 5, 1.2, 6),
+    (CLOCK, 64, 16, 2.0, 6)])
+def test_larger_3d_lattices_bit_exact(sw, model, L, q, T, sweeps):
+    """3D lattices of several tiles per axis, ragged (L = 60, 62) and not,
+    below, at and above the Ising critical temperature."""
+    run_exact_parity(sw, model, 3, L, q, T, seed=5000 + L, sweeps=sweeps)
+
+
 @pytest.mark.parametrize("dim,L,q,T", [
     (2, 32, 512, 0.9), (2, 48, 8, 1.0), (2, 37, 3, 0.7), (3, 16, 512, 2.2), (3, 20, 6, 2.0),
     (3, 9, 1024, 2.1)])
@@ -242,7 +252,7 @@ def xy_borderline(model_T, dim, L, seed, k, theta, gpu_mask, ora_mask):
 
 
 @pytest.mark.parametrize("dim,L,T,sweeps", [(2, 64, 0.89, 8), (3, 32, 2.2, 6), (3, 48, 2.0, 4),
-                                            (2, 37, 1.1, 6)])
+                                            (2, 37, 1.1, 6), (3, 64, 2.2, 3)])
 def test_xy_sweeps(sw, dim, L, T, sweeps):
     seed = 3000 + L
     h = sw.sw_create(XY, dim, L, 2, T, seed)
