@@ -210,6 +210,21 @@ cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
 int run_sweeps(sw_handle* h, int n, bool measure) {
   if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
   if (n < 0) return fail(SW_ERR_BAD_ARG, "n < 0");
+  if (n > 0 && swgb::small_lattice(h->lat)) {
+    // the whole lattice in one CTA's shared memory, many sweeps per launch
+    if (h->sweep + (uint64_t)n >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+    cudaError_t e = flush_pending(h);
+    for (int done = 0; e == cudaSuccess && done < n;) {
+      const int chunk = n - done < 256 ? n - done : 256;
+      e = swgb::launch_sweeps_small(h->lat, h->meas, (uint32_t)h->sweep, chunk, measure, h->stream);
+      if (e == cudaSuccess) {
+        h->sweep += (uint64_t)chunk;
+        done += chunk;
+      }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    return SW_OK;
+  }
   for (int s = 0; s < n; ++s) {
     if (h->sweep >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
     const uint32_t k = (uint32_t)(++h->sweep);

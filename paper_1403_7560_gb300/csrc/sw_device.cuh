@@ -396,21 +396,12 @@ __device__ __forceinline__ void finalize_record(const Lattice& lat, const Measur
   commit_record<NW>(lat, mb, sweep, M, E, S2, mx, my, exy, s_ri);
 }
 
-// Record of `sweep` from its gathered sums plus the sweep's cluster count
-// (slots reset), and the FP64 accumulators.  Called by all threads of one
-// block; thread 0 writes.
-template <int NW>
-__device__ __forceinline__ void commit_record(const Lattice& lat, const Measure& mb, uint32_t sweep,
-                                              long long M, long long E, long long S2, double mx,
-                                              double my, double exy, long long* s_ri) {
-  long long nc = 0;
-  unsigned long long* ncl_slots = mb.nclusters + kSlots * (sweep & 1u);
-  for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {
-    nc += (long long)__ldcg(&ncl_slots[k]);
-    ncl_slots[k] = 0ull;
-  }
-  const long long ncl = block_combine<NW>(warp_sum(nc), s_ri);
-  if (threadIdx.x != 0) return;
+// The record of `sweep` from its sums and cluster count, and the update of
+// the FP64 accumulators acc[6] (global, or a shared copy).  Called by one
+// thread.
+__device__ __forceinline__ void write_record(const Lattice& lat, const Measure& mb, uint32_t sweep,
+                                             long long M, long long E, long long S2, double mx, double my,
+                                             double exy, long long ncl, double* acc) {
   double M2, Ed;
   if (lat.model == kIsing) {
     M2 = __dmul_rn((double)M, (double)M);
@@ -434,13 +425,30 @@ __device__ __forceinline__ void commit_record(const Lattice& lat, const Measure&
   rec->e_xy = exy;
   rec->M2 = M2;
   rec->Ed = Ed;
-  double* acc = mb.acc;
   acc[0] = __dadd_rn(acc[0], 1.0);
   acc[1] = __dadd_rn(acc[1], M2);
   acc[2] = __dadd_rn(acc[2], __dmul_rn(M2, M2));
   acc[3] = __dadd_rn(acc[3], Ed);
   acc[4] = __dadd_rn(acc[4], __dmul_rn(Ed, Ed));
   acc[5] = __dadd_rn(acc[5], (double)ncl);
+}
+
+// Record of `sweep` from its gathered sums plus the sweep's cluster count
+// (slots reset), and the FP64 accumulators.  Called by all threads of one
+// block; thread 0 writes.
+template <int NW>
+__device__ __forceinline__ void commit_record(const Lattice& lat, const Measure& mb, uint32_t sweep,
+                                              long long M, long long E, long long S2, double mx,
+                                              double my, double exy, long long* s_ri) {
+  long long nc = 0;
+  unsigned long long* ncl_slots = mb.nclusters + kSlots * (sweep & 1u);
+  for (int k = threadIdx.x; k < kSlots; k += blockDim.x) {
+    nc += (long long)__ldcg(&ncl_slots[k]);
+    ncl_slots[k] = 0ull;
+  }
+  const long long ncl = block_combine<NW>(warp_sum(nc), s_ri);
+  if (threadIdx.x != 0) return;
+  write_record(lat, mb, sweep, M, E, S2, mx, my, exy, ncl, mb.acc);
 }
 
 }  // namespace dev

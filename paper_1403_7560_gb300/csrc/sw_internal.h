@@ -152,6 +152,14 @@ cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cud
 cudaError_t flush_pending(struct ::sw_handle* h);
 // Bytes of the small per-handle buffers (records, sums, accumulators).
 size_t handle_block_bytes();
+// Small Ising/Potts lattices (sw_small.cu): whole sweeps by one CTA with
+// the lattice in shared memory, n sweeps per launch, records written as
+// the tiled path writes them.
+constexpr int kSmallSites = 8192;
+size_t small_layout_bytes_max();
+bool small_lattice(const Lattice& lat);
+cudaError_t launch_sweeps_small(const Lattice& lat, const Measure& m, uint32_t sweep0, int n, bool measure,
+                                cudaStream_t st);
 // Waits for the handle's asynchronous uploads and downloads (no-op if none).
 cudaError_t wait_io(sw_handle* h);
 // Frees the asynchronous I/O streams, events and buffers.

@@ -1,0 +1,257 @@
+// Small Ising/Potts lattices (N <= kSmallSites): whole sweeps by one CTA
+// with the lattice in shared memory, n sweeps per launch.
+//
+// The tiled path pays four kernel launches and a global merge per sweep,
+// which for a lattice of a few thousand sites is nearly all of the time.
+// Here one CTA of 1024 threads keeps the spins, the bond planes and a
+// union-find forest over every site in shared memory and loops over the
+// sweeps: step (1) bonds with the same bit-sliced Philox words as the tiled
+// path (equality masks by warp ballots, a thread per row word and
+// direction for the Bernoulli words), step (2) the union-find of the tiled
+// path over the whole periodic lattice (every site's parent is its x-run
+// start, then a thread per row word joins the runs bonded to the next row
+// word and to the +y / +z rows; the smallest index becomes the root, so
+// labels are canonical), step (3) every site takes its root's draw (the
+// same draw definitions), and the new state is measured into the same
+// per-sweep record and FP64 accumulators.  After the last sweep the spins, that sweep's bond planes
+// and a forest of (root, marker, draw) words are written back, so every
+// readout call sees the same state as after tiled sweeps.
+#include <string>
+
+#include "../../include/sw.h"
+#include "sw_device.cuh"
+
+namespace swgb {
+namespace {
+
+using namespace dev;
+
+constexpr int kSmallThreads = 1024, kSmallWarps = kSmallThreads / 32;
+
+struct SmallLayout {
+  size_t par, planes, draws, starts, spins, pdraw, total;
+};
+
+SmallLayout small_layout(const Lattice& lat, bool potts) {
+  const size_t rw = (size_t)lat.R * (size_t)lat.W;
+  SmallLayout s;
+  s.par = 0;
+  s.planes = s.par + 4 * (size_t)lat.N;
+  s.draws = s.planes + 4 * (size_t)lat.dim * rw;
+  s.starts = s.draws + 4 * rw;
+  s.spins = s.starts + 4 * rw;
+  s.pdraw = s.spins + (size_t)lat.N;
+  s.total = s.pdraw + (potts ? (size_t)lat.N : 0);
+  s.total = (s.total + 15) & ~(size_t)15;
+  return s;
+}
+
+template <int D, bool POTTS>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    k_sweep_small(const __grid_constant__ Lattice lat, const __grid_constant__ Measure mb, uint32_t sweep0,
+                  int n, int measure, SmallLayout lay) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_ri[kSmallWarps];
+  __shared__ unsigned int s_hist[256];
+  __shared__ double s_acc[6];  // the FP64 accumulators, written back at the end
+  uint32_t* par = reinterpret_cast<uint32_t*>(smem + lay.par);
+  uint32_t* pl = reinterpret_cast<uint32_t*>(smem + lay.planes);
+  uint32_t* dw = reinterpret_cast<uint32_t*>(smem + lay.draws);
+  uint32_t* ss = reinterpret_cast<uint32_t*>(smem + lay.starts);  // x-run starts of each row word
+  uint8_t* sp = smem + lay.spins;
+  uint8_t* pd = smem + lay.pdraw;
+  const uint32_t N = lat.N, L = (uint32_t)lat.L, W = (uint32_t)lat.W, RW = lat.R * W;
+  const uint32_t tid = threadIdx.x;
+  const int q = lat.q, sb = lat.sbits, shift = sb + 1;
+  const bool two_state = lat.dq == 2;
+  const uint32_t lr_bit = 1u << sb;
+  const uint8_t* gs = static_cast<const uint8_t*>(lat.spins);
+  for (uint32_t i = tid; i < N; i += kSmallThreads) sp[i] = gs[i];
+  if (tid < 6) s_acc[tid] = mb.acc[tid];
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+
+  for (int s = 0; s < n; ++s) {
+    const uint32_t sweep = sweep0 + (uint32_t)s + 1u;
+    const bool last = s + 1 == n;
+    __syncthreads();
+    // step (1a): equality masks, a warp per row word (lane per site, ballots)
+    for (uint32_t g = warp; g < RW; g += kSmallWarps) {
+      const uint32_t row = g / W, x = 32u * (g % W) + lane;
+      const uint32_t y = row % L, z = row / L;
+      bool q0 = false, q1 = false, q2 = false;
+      if (x < L) {
+        const uint8_t si = sp[row * L + x];
+        q0 = sp[row * L + (x + 1u == L ? 0u : x + 1u)] == si;
+        q1 = sp[((y + 1u == L ? 0u : y + 1u) + L * z) * L + x] == si;
+        if (D == 3) q2 = sp[(y + L * (z + 1u == L ? 0u : z + 1u)) * L + x] == si;
+      }
+      const uint32_t b0 = __ballot_sync(kFull, q0), b1 = __ballot_sync(kFull, q1), b2 = __ballot_sync(kFull, q2);
+      if (lane < (uint32_t)D) pl[lane * RW + g] = lane == 0 ? b0 : lane == 1 ? b1 : b2;
+    }
+    __syncthreads();
+    // step (1b): Bernoulli words, a thread per (row word, direction); the
+    // two-state draw words
+    for (uint32_t c = tid; c < (uint32_t)D * RW; c += kSmallThreads) {
+      const uint32_t d = c / RW, g = c % RW;
+      const uint32_t e = pl[c];
+      pl[c] = e ? (e & bernoulli_word(g, sweep, (int)d, lat.t_bond, e, lat.rk)) : 0u;
+    }
+    if (two_state)
+      for (uint32_t g = tid; g < RW; g += kSmallThreads) dw[g] = philox(g, sweep, kDraw, 1u, lat.rk).x;
+    if (POTTS && !two_state) {
+      // Potts draw of every site: word (i & 3) of Philox(i >> 2, sweep, DRAW, 0)
+      for (uint32_t c = tid; 4u * c < N; c += kSmallThreads) {
+        const uint4 w = philox(c, sweep, kDraw, 0u, lat.rk);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (4u * c + (uint32_t)k < N) pd[4u * c + (uint32_t)k] = (uint8_t)draw_value(word_of(w, k), (uint32_t)lat.dq);
+      }
+    }
+    __syncthreads();
+    // step (2a): every site's parent is the start of its x-run inside its
+    // row word (a warp per row word, lane per site)
+    for (uint32_t g = warp; g < RW; g += kSmallWarps) {
+      const uint32_t row = g / W, x0 = 32u * (g % W);
+      const int nvalid = (int)min(32u, L - x0);
+      const uint32_t vmask = nvalid >= 32 ? kFull : ((1u << nvalid) - 1u);
+      const uint32_t S = ~((pl[g] & (vmask >> 1)) << 1) & vmask;
+      if (lane == 0) ss[g] = S;
+      if ((int)lane < nvalid) par[row * L + x0 + lane] = row * L + x0 + run_start(S, (int)lane);
+    }
+    __syncthreads();
+    // step (2b): a thread per row word joins the runs bonded to the next row
+    // word along x (or around), to the +y row and to the +z row; runs
+    // already joined through the previous bit are skipped
+    for (uint32_t g = tid; g < RW; g += kSmallThreads) {
+      const uint32_t row = g / W, xw = g % W, x0 = 32u * xw;
+      const uint32_t y = row % L, z = row / L;
+      const int nvalid = (int)min(32u, L - x0);
+      const uint32_t vmask = nvalid >= 32 ? kFull : ((1u << nvalid) - 1u);
+      const uint32_t A0 = pl[g], X = A0 & (vmask >> 1), S = ss[g], base = row * L + x0;
+      if ((A0 >> (nvalid - 1)) & 1u) {
+        const uint32_t i = base + (uint32_t)(nvalid - 1);
+        sunion(par, base + run_start(S, nvalid - 1), x0 + (uint32_t)nvalid == L ? row * L : i + 1u, lat.err);
+      }
+#pragma unroll
+      for (int d = 1; d < D; ++d) {
+        const uint32_t rown = (d == 1) ? (y + 1u == L ? 0u : y + 1u) + L * z
+                                       : y + L * (z + 1u == L ? 0u : z + 1u);
+        const uint32_t gn = rown * W + xw, Yd = pl[d * RW + g];
+        if (!Yd) continue;
+        const uint32_t Xn = pl[gn] & (vmask >> 1), Sn = ss[gn], basen = rown * L + x0;
+        uint32_t U = Yd & ~((Yd & X & Xn) << 1);
+        while (U) {
+          const int b = __ffs(U) - 1;
+          U &= U - 1u;
+          sunion(par, base + run_start(S, b), basen + run_start(Sn, b), lat.err);
+        }
+      }
+    }
+    __syncthreads();
+    // step (3): every site takes its root's draw; roots counted
+    long long roots = 0;
+    for (uint32_t g = warp; g < RW; g += kSmallWarps) {
+      const uint32_t row = g / W, x = 32u * (g % W) + lane;
+      if (x >= L) continue;
+      const uint32_t i = row * L + x;
+      const uint32_t r = sfind(par, i);
+      if (r == i) ++roots;
+      const uint32_t xr = r % L, gr = (r / L) * W + (xr >> 5);
+      const uint32_t v = two_state ? (dw[gr] >> (xr & 31u)) & 1u : pd[r];
+      sp[i] = POTTS ? (uint8_t)v : (uint8_t)(v ? (int8_t)-1 : (int8_t)1);
+      if (last) {
+        const uint32_t own = two_state ? (dw[g] >> lane) & 1u : pd[i];
+        lat.forest[i] = (r << shift) | (r == i ? lr_bit : 0u) | own;
+      }
+    }
+    if (!measure) continue;
+    // the new state's record: M, E (Potts: E and the histogram), roots
+    if (POTTS) {
+      __syncthreads();
+      for (int k = tid; k < 256; k += kSmallThreads) s_hist[k] = 0u;
+    }
+    __syncthreads();
+    long long m = 0, en = 0;
+    for (uint32_t g = warp; g < RW; g += kSmallWarps) {
+      const uint32_t row = g / W, x = 32u * (g % W) + lane;
+      if (x >= L) continue;
+      const uint32_t y = row % L, z = row / L, i = row * L + x;
+      uint32_t j[3];
+      j[0] = x + 1u == L ? i - x : i + 1u;
+      j[1] = y + 1u == L ? i - y * L : i + L;
+      j[2] = (D == 3) ? (z + 1u == L ? i - z * L * L : i + L * L) : i;
+      if (POTTS) {
+        const uint32_t si = sp[i];
+        atomicAdd(&s_hist[si], 1u);
+#pragma unroll
+        for (int d = 0; d < D; ++d) en += sp[j[d]] != si;
+      } else {
+        const int si = (int8_t)sp[i];
+        m += si;
+#pragma unroll
+        for (int d = 0; d < D; ++d) en -= si * (int)(int8_t)sp[j[d]];
+      }
+    }
+    long long s2 = 0;
+    if (POTTS) {
+      __syncthreads();
+      if (tid < (uint32_t)q) s2 = (long long)s_hist[tid] * (long long)s_hist[tid];
+    }
+    const long long M = block_combine<kSmallWarps>(warp_sum(m), s_ri);
+    const long long E = block_combine<kSmallWarps>(warp_sum(en), s_ri);
+    const long long S2 = block_combine<kSmallWarps>(warp_sum(s2), s_ri);
+    const long long ncl = block_combine<kSmallWarps>(warp_sum(roots), s_ri);
+    if (tid == 0) write_record(lat, mb, sweep, M, E, S2, 0.0, 0.0, 0.0, ncl, s_acc);
+  }
+  __syncthreads();
+  uint8_t* out = static_cast<uint8_t*>(lat.spins);
+  for (uint32_t i = tid; i < N; i += kSmallThreads) out[i] = sp[i];
+  for (uint32_t w = tid; w < (uint32_t)D * RW; w += kSmallThreads) lat.planes[w] = pl[w];
+  if (tid < 6) mb.acc[tid] = s_acc[tid];
+}
+
+template <int D, bool POTTS>
+cudaError_t launch_small_t(const Lattice& lat, const Measure& m, uint32_t sweep0, int n, bool measure,
+                           cudaStream_t st) {
+  const SmallLayout lay = small_layout(lat, POTTS);
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured_device != dev) {
+    e = cudaFuncSetAttribute(k_sweep_small<D, POTTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)small_layout_bytes_max());
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  k_sweep_small<D, POTTS><<<1, kSmallThreads, lay.total, st>>>(lat, m, sweep0, n, measure ? 1 : 0, lay);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t small_layout_bytes_max() {
+  // N <= kSmallSites, bond planes of at most N / 8 words per direction
+  // beyond N / 32 (rows padded to words), and Potts draws
+  return (size_t)kSmallSites * 4 + 3 * 4 * (size_t)kSmallSites / 4 + 4 * (size_t)kSmallSites / 4 +
+         2 * (size_t)kSmallSites + 16;
+}
+
+bool small_lattice(const Lattice& lat) {
+  if (lat.model != kIsing && lat.model != kPotts) return false;
+  // measured on the GB300: faster than the tiled path up to 8192 sites in 2D
+  // (L <= 90) and 4096 in 3D (L <= 16)
+  if (lat.N > (uint32_t)(lat.dim == 2 ? kSmallSites : kSmallSites / 2)) return false;
+  return small_layout(lat, lat.model == kPotts).total <= small_layout_bytes_max();
+}
+
+cudaError_t launch_sweeps_small(const Lattice& lat, const Measure& m, uint32_t sweep0, int n, bool measure,
+                                cudaStream_t st) {
+  const bool potts = lat.model == kPotts;
+  if (lat.dim == 2) return potts ? launch_small_t<2, true>(lat, m, sweep0, n, measure, st)
+                                 : launch_small_t<2, false>(lat, m, sweep0, n, measure, st);
+  return potts ? launch_small_t<3, true>(lat, m, sweep0, n, measure, st)
+               : launch_small_t<3, false>(lat, m, sweep0, n, measure, st);
+}
+
+}  // namespace swgb
