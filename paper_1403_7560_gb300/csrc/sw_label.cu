@@ -378,17 +378,35 @@ __global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattic
     const int x0 = 32 * (int)(t % nbx), y0 = BY * (int)((t / nbx) % nby), z0 = BZ * (int)(t / (nbx * nby));
     const int nx = min(32, L - x0), ny = min(BY, L - y0), nz = (D == 3) ? min(BZ, L - z0) : 1;
     __syncthreads();  // the previous block's values are no longer read
-    for (int e = threadIdx.x; e < NBOX; e += 256) {
-      const int xx = e % HX, r = e / HX, yy = r % HY, zz = r / HY;
-      if (xx > nx || yy > ny || zz > nz) continue;  // beyond the valid sites and their halo
-      int gx = x0 + xx, gy = y0 + yy, gz = (D == 3) ? z0 + zz : 0;
-      if (gx >= L) gx -= L;
+    // a warp per halo row (yy, zz), lanes along x; then the +x halo column
+    // (entry 32 of every row) a thread per row
+    for (int hr = warp; hr < HY * HZ; hr += NW) {
+      const int yy = hr % HY, zz = hr / HY;
+      if (yy > ny || zz > nz || lane > nx) continue;  // beyond the valid sites and their halo
+      int gy = y0 + yy, gz = (D == 3) ? z0 + zz : 0;
       if (gy >= L) gy -= L;
       if (gz >= L) gz -= L;
+      int gx = x0 + lane;
+      if (gx >= L) gx -= L;
       float sn, cs;
-      sincosf(__fsub_rn(__ldg(&th[(uint32_t)gx + (uint32_t)L * ((uint32_t)gy + (uint32_t)L * (uint32_t)gz)]), phi),
-              &sn, &cs);
-      sv[e] = make_float2(cs, sn);
+      sincosf(__fsub_rn(__ldg(&th[(uint32_t)gx + (uint32_t)L * ((uint32_t)gy + (uint32_t)L * (uint32_t)gz)]),
+                        phi), &sn, &cs);
+      sv[hr * HX + lane] = make_float2(cs, sn);
+    }
+    if (nx == 32) {
+      for (int hr = threadIdx.x; hr < HY * HZ; hr += 256) {
+        const int yy = hr % HY, zz = hr / HY;
+        if (yy > ny || zz > nz) continue;
+        int gy = y0 + yy, gz = (D == 3) ? z0 + zz : 0;
+        if (gy >= L) gy -= L;
+        if (gz >= L) gz -= L;
+        int gx = x0 + 32;
+        if (gx >= L) gx -= L;
+        float sn, cs;
+        sincosf(__fsub_rn(__ldg(&th[(uint32_t)gx + (uint32_t)L * ((uint32_t)gy + (uint32_t)L * (uint32_t)gz)]),
+                          phi), &sn, &cs);
+        sv[hr * HX + 32] = make_float2(cs, sn);
+      }
     }
     __syncthreads();
     for (int rr = warp; rr < BY * BZ; rr += NW) {
