@@ -15,7 +15,8 @@
  *       SW_ISING  int8_t  +1 / -1
  *       SW_POTTS  uint8_t 0 .. q-1
  *       SW_XY     float   angle theta in [0, 2 pi)
- *       SW_CLOCK  uint16  clock state p in [0, q), angle 2 pi p / q
+ *       SW_CLOCK  uint16  clock state p in [0, q), angle 2 pi p / q (a state
+ *                         set outside [0, q) is read mod q)
  *   - Bond bit-planes: plane d (0 <= d < dim) holds bond (i, i + e_d); each
  *     row (fixed y, z) is padded to W = ceil(L/32) uint32 words; the bit of
  *     site i is word d*R*W + row*W + (x >> 5), bit (x & 31), with

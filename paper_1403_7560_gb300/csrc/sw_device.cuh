@@ -112,6 +112,13 @@ __device__ __forceinline__ int wrap_mod(int v, int m) {
   return v < 0 ? v + m : (v >= m ? v - m : v);
 }
 
+// A clock state as an index into the model's tables: states set by the
+// caller outside [0, q) are reduced mod q instead of indexing past a table
+// (the branch is never taken for valid states).
+__device__ __forceinline__ int clock_state(uint32_t p, int q) {
+  return p < (uint32_t)q ? (int)p : (int)(p % (uint32_t)q);
+}
+
 // Highest set bit of `starts` at or below bit b (the start of b's x-run).
 __device__ __forceinline__ uint32_t run_start(uint32_t starts, int b) {
   return 31u - __clz(starts & (kFull >> (31 - b)));

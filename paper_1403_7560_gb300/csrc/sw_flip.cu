@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
         if (draw) {
           uint16_t* sp = static_cast<uint16_t*>(lat.spins);
           const int q = lat.q;
-          sp[i] = (uint16_t)wrap_mod((int)s_mirror - (int)sp[i], q);
+          sp[i] = (uint16_t)wrap_mod((int)s_mirror - clock_state(sp[i], q), q);
         }
       } else if (draw) {
         float* th = static_cast<float*>(lat.spins);

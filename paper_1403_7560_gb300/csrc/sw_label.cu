@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
       jn[0] = (x + 1 == L) ? i - (uint32_t)x : i + 1u;
       jn[1] = (y + 1 == (uint32_t)L) ? i - y * L : i + (uint32_t)L;
       jn[2] = (D == 3) ? ((z + 1 == (uint32_t)L) ? i - z * L * L : i + (uint32_t)L * L) : 0u;
-      const int pi = sp[i];
+      const int pi = clock_state(sp[i], q);
       const int ki = wrap_mod(2 * pi - mirror, q2);
       if (MEASURE) {
         cx += __ldg(&mb.cfix[pi]);
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
       }
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const int pj = sp[jn[d]];
+        const int pj = clock_state(sp[jn[d]], q);
         const int kj = wrap_mod(2 * pj - mirror, q2);
         a |= (uint32_t)(word_of(w, d) < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj])) << d;
         if (MEASURE) eb += __ldg(&mb.cfix[wrap_mod(pi - pj, q)]);

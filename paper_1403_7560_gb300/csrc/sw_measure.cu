@@ -80,11 +80,11 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
         // fixed-point sums: C[p_i], S[p_i] and C[(p_i - p_j) mod q]
         const uint16_t* sp = static_cast<const uint16_t*>(lat.spins);
         const int q = lat.q;
-        const int pi = sp[i];
+        const int pi = clock_state(sp[i], q);
         m += __ldg(&mb.cfix[pi]);
         e += __ldg(&mb.cfix[q + pi]);
 #pragma unroll
-        for (int d = 0; d < D; ++d) cb += __ldg(&mb.cfix[wrap_mod(pi - (int)sp[jn[d]], q)]);
+        for (int d = 0; d < D; ++d) cb += __ldg(&mb.cfix[wrap_mod(pi - clock_state(sp[jn[d]], q), q)]);
       } else {
         const float* th = static_cast<const float*>(lat.spins);
         const float ti = th[i];

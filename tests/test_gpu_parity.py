@@ -108,6 +108,29 @@ def test_clock_sweeps_bit_exact(sw, dim, L, q, T):
     run_exact_parity(sw, CLOCK, dim, L, q, T, seed=4000 + L, sweeps=10)
 
 
+def test_clock_states_out_of_range_are_read_mod_q(sw):
+    """States set outside [0, q) index no table out of range: the sweep runs
+    as on the states mod q (bit-exact), unflipped sites keep their raw value."""
+    dim, L, q, T, seed = 3, 24, 12, 2.0, 31
+    rng = np.random.default_rng(5)
+    raw = rng.integers(0, 65536, size=L ** dim).astype(np.uint16)
+    h = sw.sw_create(CLOCK, dim, L, q, T, seed)
+    o = oracle.Oracle(CLOCK, dim, L, q, T, seed)
+    try:
+        sw.sw_set_spins(h, raw)
+        o.spins = (raw % q).astype(np.uint16)
+        for k in range(1, 5):
+            sw.sw_sweep(h, 1)
+            o.sweep(1)
+            assert np.array_equal(sw.sw_get_bonds(h), o.planes), k
+            assert np.array_equal(sw.sw_get_spins(h) % q, o.spins), k
+            rec, ref = sw.sw_get_series(h, k, 1)[0], o.last_record()
+            assert (rec["mx"], rec["my"], rec["e_xy"]) == (ref["mx"], ref["my"], ref["e_xy"]), k
+    finally:
+        sw.sw_destroy(h)
+        o.close()
+
+
 def test_clock_config_3d_L64_q512(sw):
     """3D clock q=512 (Sec. 3's XY runs) near its critical temperature."""
     run_exact_parity(sw, CLOCK, 3, 64, 512, 2.20184, seed=1002, sweeps=3)
