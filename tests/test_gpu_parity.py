@@ -211,6 +211,44 @@ def test_config_3d_ising_L256_first_sweeps(sw):
     run_exact_parity(sw, model, dim, L, q, T, seed, sweeps=2)
 
 
+@pytest.mark.parametrize("dim,L,T", [(3, 1024, 1 / 0.2216546), (2, 32768, 2.269185)])
+def test_maximum_ising_lattice(sw, dim, L, T):
+    """The largest Ising lattice sw_create accepts (N = 2^30 sites, the forest
+    word's limit): one sweep, then properties that hold at any size, checked
+    on every site or on a large sample (the oracle cannot run this size)."""
+    N = L ** dim
+    assert N == 1 << 30
+    h = sw.sw_create(ISING, dim, L, 2, T, 7)
+    try:
+        s0 = sw.sw_get_spins(h)
+        sw.sw_sweep(h, 1)
+        planes = sw.sw_get_bonds(h)
+        s1 = sw.sw_get_spins(h)
+        lab = sw.sw_get_labels(h)
+        rec = sw.sw_get_series(h, 1, 1)[0]
+        assert rec["M"] == int(s1.sum(dtype=np.int64))
+        roots = np.flatnonzero(lab == np.arange(N, dtype=np.int32))
+        assert rec["nclusters"] == roots.size
+        rng = np.random.default_rng(11)
+        i = rng.integers(0, N, size=200_000)
+        assert np.all(lab[i] <= i) and np.all(lab[lab[i]] == lab[i])   # canonical roots
+        W, R = (L + 31) // 32, N // L
+        x, row = i % L, i // L
+        y, z = row % L, row // L
+        for d in range(dim):
+            bit = (planes[d * R * W + row * W + (x >> 5)] >> (x & 31).astype(np.uint32)) & 1
+            j = [np.where(x + 1 == L, i - x, i + 1),
+                 np.where(y + 1 == L, i - y * L, i + L),
+                 np.where(z + 1 == L, i - z * L * L, i + L * L)][d]
+            on = bit.astype(bool)
+            assert on.any()
+            assert np.all(s0[i[on]] == s0[j[on]])        # bonds join equal spins
+            assert np.all(lab[i[on]] == lab[j[on]])      # bonded sites share a cluster
+            assert np.all(s1[i[on]] == s1[j[on]])        # and the cluster's new spin
+    finally:
+        sw.sw_destroy(h)
+
+
 # ---------------------------------------------------------------- labels
 @pytest.mark.parametrize("dim,L", [(2, 4), (2, 31), (2, 64), (2, 97), (2, 200), (3, 4), (3, 8),
                                    (3, 13), (3, 32), (3, 41)])
