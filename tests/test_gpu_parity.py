@@ -249,6 +249,14 @@ def test_maximum_ising_lattice(sw, dim, L, T):
         sw.sw_destroy(h)
 
 
+def test_maximum_potts_q256_lattice(sw):
+    """Potts q=256 needs 8 draw bits, so the forest word limits N to 2^23:
+    3D L=203 (8,365,427 sites) is the largest cube, bit-exact for 2 sweeps."""
+    with pytest.raises(sw.SwError):
+        sw.sw_create(POTTS, 3, 204, 256, 0.5, 1)
+    run_exact_parity(sw, POTTS, 3, 203, 256, 0.5, seed=6203, sweeps=2)
+
+
 # ---------------------------------------------------------------- labels
 @pytest.mark.parametrize("dim,L", [(2, 4), (2, 31), (2, 64), (2, 97), (2, 200), (3, 4), (3, 8),
                                    (3, 13), (3, 32), (3, 41)])
