@@ -217,11 +217,13 @@ def run_reference(args):
 # The other single-lattice workloads of the measurement plan, timed briefly
 # beside the headline (CUDA events per measured sweep, L2 flushed between
 # sweeps): 3D XY L=256 at K=0.4541652 (seed 1002), the paper's discretised
-# XY (the q=512 clock model) at the same temperature, and the small 2D Ising
-# L=64 lattice at T=2.269185 (seed 1000), which is launch-latency bound.
+# XY (the q=512 clock model) at the same temperature, the 2D Ising L=4096
+# lattice at T=2.269185, and the small 2D Ising L=64 lattice at the same T
+# (seed 1000), which is latency bound.
 OTHER_WORKLOADS = [
     ("xy3d_L256", 2, 3, 256, 2, 1.0 / 0.4541652, 1002, 20, 50),
     ("clock3d_q512_L256", 3, 3, 256, 512, 1.0 / 0.4541652, 1002, 20, 50),
+    ("ising2d_L4096", 0, 2, 4096, 2, 2.269185, 1000, 20, 50),
 ]
 # the 2D Ising L=64 configuration as specified: 200 discarded, then 1000
 # measured sweeps in one sw_sweep call (events around the call)
