@@ -9,6 +9,16 @@ namespace swgb {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Programmatic dependent launch.  The kernels of a sweep are launched with
+// programmatic stream serialisation (launch_pdl): the launch of a kernel is
+// processed while its predecessor runs, and pdl_wait() blocks until the
+// predecessor has completed and its writes are visible (it returns at once
+// for a kernel launched without the attribute).  Every such kernel calls
+// pdl_wait() before its first global memory access.  No kernel triggers its
+// successor early (griddepcontrol.launch_dependents): successors resident
+// ahead of time, waiting, made the sweep slower on the GB300.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr int kErrTimeout = -4;
 
 // Philox purposes (third counter word).

@@ -55,6 +55,7 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   const uint32_t plane = lat.R * (uint32_t)lat.W;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) s_n = 0;
+  pdl_wait();
 
   // this thread's face bonds: bond bits first, then both forest words
   uint32_t ii[NC], jj[NC], a[NC], b[NC];
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(kTileThreads, 8) k_merge(Lattice lat) {
 template <int D>
 __global__ void __launch_bounds__(kTileThreads, 8) k_merge_batch(BatchView bv) {
   __shared__ MergeSmem<D> sm;
+  pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   merge_tile<D>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
 }
@@ -162,6 +164,7 @@ __device__ __forceinline__ void compress_tile(const Lattice& lat, uint32_t t) {
 __global__ void __launch_bounds__(kFlipThreads, 8) k_compress(Lattice lat, Measure mb, uint32_t finalize) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
+  pdl_wait();
   if (finalize != 0u && blockIdx.x == 0) finalize_record<kFlipWarps>(lat, mb, finalize, s_red, s_rd);
   const uint32_t ntiles = (uint32_t)(lat.ntx * lat.nty * lat.ntz);
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) compress_tile(lat, t);
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(kFlipThreads, 8) k_compress(Lattice lat, Measu
 __global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
+  pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const uint32_t step = *bv.step;
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
     }
     __syncthreads();
   }
+  pdl_wait();
   const int sb = lat.sbits, shift = sb + 1;
   const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -252,6 +257,7 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
   constexpr int TY = Tile<D>::TY, ROWS = Tile<D>::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
   constexpr int B = 8;
   __shared__ long long s_red[NW];
+  pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   const Lattice& lat = m.lat;
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
@@ -292,7 +298,10 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
     atomicAdd(m.meas.nclusters + kSlots * (sweep & 1u) + (tile % kSlots), (unsigned long long)tot);
 }
 
-__global__ void k_advance(uint32_t* step) { *step += 1u; }
+__global__ void k_advance(uint32_t* step) {
+  pdl_wait();
+  *step += 1u;
+}
 
 __global__ void __launch_bounds__(256) k_labels_out(Lattice lat, int32_t* out) {
   const int shift = lat.sbits + 1;
@@ -315,9 +324,8 @@ int merge_list_capacity(int dim) { return dim == 2 ? MergeShape<2>::kMax : Merge
 
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  if (lat.dim == 2) k_merge<2><<<g, kTileThreads, 0, st>>>(lat);
-  else k_merge<3><<<g, kTileThreads, 0, st>>>(lat);
-  return cudaGetLastError();
+  if (lat.dim == 2) return launch_pdl(k_merge<2>, g, kTileThreads, st, lat);
+  return launch_pdl(k_merge<3>, g, kTileThreads, st, lat);
 }
 
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
@@ -326,26 +334,26 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
   if (g > kFlipBlocks) g = kFlipBlocks;
   if (g == 0) g = 1;
   const unsigned ntiles = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  k_compress<<<ntiles, kFlipThreads, 0, st>>>(lat, m, finalize);
-  if (model == kIsing) k_apply<kIsing><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
-  else if (model == kPotts) k_apply<kPotts><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
-  else if (model == kClock) k_apply<kClock><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
-  else k_apply<kXY><<<g, kFlipThreads, 0, st>>>(lat, sweep, m, count);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_compress, ntiles, kFlipThreads, st, lat, m, finalize);
+  if (e != cudaSuccess) return e;
+  if (model == kIsing) return launch_pdl(k_apply<kIsing>, g, kFlipThreads, st, lat, sweep, m, count);
+  if (model == kPotts) return launch_pdl(k_apply<kPotts>, g, kFlipThreads, st, lat, sweep, m, count);
+  if (model == kClock) return launch_pdl(k_apply<kClock>, g, kFlipThreads, st, lat, sweep, m, count);
+  return launch_pdl(k_apply<kXY>, g, kFlipThreads, st, lat, sweep, m, count);
 }
 
 cudaError_t launch_merge_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
-  if (dim == 2) k_merge_batch<2><<<ntiles, kTileThreads, 0, st>>>(bv);
-  else k_merge_batch<3><<<ntiles, kTileThreads, 0, st>>>(bv);
-  return cudaGetLastError();
+  if (dim == 2) return launch_pdl(k_merge_batch<2>, ntiles, kTileThreads, st, bv);
+  return launch_pdl(k_merge_batch<3>, ntiles, kTileThreads, st, bv);
 }
 
 cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
-  k_compress_batch<<<ntiles, kFlipThreads, 0, st>>>(bv);
-  if (dim == 2) k_apply_batch<2><<<ntiles, kFlipThreads, 0, st>>>(bv);
-  else k_apply_batch<3><<<ntiles, kFlipThreads, 0, st>>>(bv);
-  k_advance<<<1, 1, 0, st>>>(bv.step);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_compress_batch, ntiles, kFlipThreads, st, bv);
+  if (e == cudaSuccess)
+    e = (dim == 2) ? launch_pdl(k_apply_batch<2>, ntiles, kFlipThreads, st, bv)
+                   : launch_pdl(k_apply_batch<3>, ntiles, kFlipThreads, st, bv);
+  if (e == cudaSuccess) e = launch_pdl(k_advance, 1u, 1u, st, bv.step);
+  return e;
 }
 
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st) {

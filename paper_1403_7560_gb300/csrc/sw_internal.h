@@ -102,6 +102,26 @@ constexpr int kTile3Y = 16;   // 3D: 32 x 16 x 16 sites
 constexpr int kTile3Z = 16;
 constexpr int kTileThreads = 256;
 
+// Launches kernel k with programmatic stream serialisation: its launch is
+// processed while the preceding kernel in the stream runs, and it waits for
+// that kernel with griddepcontrol.wait (pdl_wait in sw_device.cuh) before
+// touching global memory.  Every kernel launched this way must make that
+// call.
+template <class... K, class... A>
+cudaError_t launch_pdl(void (*k)(K...), unsigned grid, unsigned block, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
+
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
 // Bonds that leave one tile (its +x, +y, +z faces): the most roots one
 // tile's merge can hook.

@@ -149,6 +149,9 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
     }
   }
 
+  // global memory only after the preceding kernel of the sweep is done
+  pdl_wait();
+
   // ---- phase 1: bonds, runs and draws of this thread's row word
   const int r = threadIdx.x;
   const int ry = r % TY, rz = r / TY;
@@ -320,6 +323,7 @@ __global__ void __launch_bounds__(kTileThreads, POTTS ? 4 : 5) k_label_batch(Bat
   // keys are read on every round
   __shared__ Lattice s_lat;
   static_assert(sizeof(Lattice) % 4 == 0 && sizeof(Lattice) / 4 <= kTileThreads, "lattice copy");
+  pdl_wait();
   const uint32_t b = __ldg(&bv.tile_lattice[first + blockIdx.x]);
   const uint32_t tile = __ldg(&bv.tile_index[first + blockIdx.x]);
   const BatchMember& m = bv.members[b];
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattic
   __shared__ float s_phi;
   __shared__ double s_rd[NW];
   if (threadIdx.x == 0) s_phi = xy_phi(lat, sweep);
+  pdl_wait();
   __syncthreads();
   const float phi = s_phi;
   const int L = lat.L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -476,6 +481,7 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
   __shared__ uint32_t s_mirror;
   __shared__ long long s_red[256 / 32];
   if (threadIdx.x == 0) s_mirror = clock_mirror(lat, sweep);
+  pdl_wait();
   __syncthreads();
   const int L = lat.L, lane = threadIdx.x & 31;
   const int q = lat.q, q2 = 2 * q;
@@ -527,15 +533,16 @@ cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, const Measure
   const uint32_t words = lat.R * (uint32_t)lat.W;
   unsigned g = (words + 7u) / 8u;
   if (g > 4096u) g = 4096u;
+  cudaError_t e = cudaSuccess;
   const Measure none{};
   if (lat.dim == 2) {
-    if (m) k_bonds_clock<2, true><<<g, 256, 0, st>>>(lat, sweep, *m);
-    else k_bonds_clock<2, false><<<g, 256, 0, st>>>(lat, sweep, none);
+    if (m) e = launch_pdl(k_bonds_clock<2, true>, g, 256, st, lat, sweep, *m);
+    else e = launch_pdl(k_bonds_clock<2, false>, g, 256, st, lat, sweep, none);
   } else {
-    if (m) k_bonds_clock<3, true><<<g, 256, 0, st>>>(lat, sweep, *m);
-    else k_bonds_clock<3, false><<<g, 256, 0, st>>>(lat, sweep, none);
+    if (m) e = launch_pdl(k_bonds_clock<3, true>, g, 256, st, lat, sweep, *m);
+    else e = launch_pdl(k_bonds_clock<3, false>, g, 256, st, lat, sweep, none);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz) {
@@ -551,42 +558,45 @@ void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz) {
 
 cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
+  cudaError_t e = cudaSuccess;
   const Measure none{};
   if (lat.dim == 2) {
-    if (from_mask) k_label<2, true, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
-    else k_label<2, false, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
+    if (from_mask) e = launch_pdl(k_label<2, true, 0>, g, kTileThreads, st, lat, sweep, none);
+    else e = launch_pdl(k_label<2, false, 0>, g, kTileThreads, st, lat, sweep, none);
   } else {
-    if (from_mask) k_label<3, true, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
-    else k_label<3, false, 0><<<g, kTileThreads, 0, st>>>(lat, sweep, none);
+    if (from_mask) e = launch_pdl(k_label<3, true, 0>, g, kTileThreads, st, lat, sweep, none);
+    else e = launch_pdl(k_label<3, false, 0>, g, kTileThreads, st, lat, sweep, none);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ising_tiles, uint32_t potts_tiles,
                                cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
   if (ising_tiles) {
-    if (dim == 2) k_label_batch<2, false><<<ising_tiles, kTileThreads, 0, st>>>(bv, 0u);
-    else k_label_batch<3, false><<<ising_tiles, kTileThreads, 0, st>>>(bv, 0u);
+    if (dim == 2) e = launch_pdl(k_label_batch<2, false>, ising_tiles, kTileThreads, st, bv, 0u);
+    else e = launch_pdl(k_label_batch<3, false>, ising_tiles, kTileThreads, st, bv, 0u);
   }
-  if (potts_tiles) {
-    if (dim == 2) k_label_batch<2, true><<<potts_tiles, kTileThreads, 0, st>>>(bv, ising_tiles);
-    else k_label_batch<3, true><<<potts_tiles, kTileThreads, 0, st>>>(bv, ising_tiles);
+  if (e == cudaSuccess && potts_tiles) {
+    if (dim == 2) e = launch_pdl(k_label_batch<2, true>, potts_tiles, kTileThreads, st, bv, ising_tiles);
+    else e = launch_pdl(k_label_batch<3, true>, potts_tiles, kTileThreads, st, bv, ising_tiles);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Measure& m,
                                   cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
+  cudaError_t e = cudaSuccess;
   const bool potts = lat.model == kPotts;
   if (lat.dim == 2) {
-    if (potts) k_label<2, false, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
-    else k_label<2, false, 1><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
+    if (potts) e = launch_pdl(k_label<2, false, 2>, g, kTileThreads, st, lat, sweep, m);
+    else e = launch_pdl(k_label<2, false, 1>, g, kTileThreads, st, lat, sweep, m);
   } else {
-    if (potts) k_label<3, false, 2><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
-    else k_label<3, false, 1><<<g, kTileThreads, 0, st>>>(lat, sweep, m);
+    if (potts) e = launch_pdl(k_label<3, false, 2>, g, kTileThreads, st, lat, sweep, m);
+    else e = launch_pdl(k_label<3, false, 1>, g, kTileThreads, st, lat, sweep, m);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, const Measure* m, int* blocks,
@@ -596,16 +606,17 @@ cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, const Measure* m
                           ? (uint32_t)lat.W * (uint32_t)((lat.L + XYBlock<2>::BY - 1) / XYBlock<2>::BY)
                           : (uint32_t)lat.W * ny * (uint32_t)((lat.L + XYBlock<3>::BZ - 1) / XYBlock<3>::BZ);
   const unsigned g = nb < (uint32_t)kMeasureBlocks ? (nb ? nb : 1u) : (unsigned)kMeasureBlocks;
+  cudaError_t e = cudaSuccess;
   const Measure none{};
   if (lat.dim == 2) {
-    if (m) k_bonds_xy<2, true><<<g, 256, 0, st>>>(lat, sweep, *m);
-    else k_bonds_xy<2, false><<<g, 256, 0, st>>>(lat, sweep, none);
+    if (m) e = launch_pdl(k_bonds_xy<2, true>, g, 256, st, lat, sweep, *m);
+    else e = launch_pdl(k_bonds_xy<2, false>, g, 256, st, lat, sweep, none);
   } else {
-    if (m) k_bonds_xy<3, true><<<g, 256, 0, st>>>(lat, sweep, *m);
-    else k_bonds_xy<3, false><<<g, 256, 0, st>>>(lat, sweep, none);
+    if (m) e = launch_pdl(k_bonds_xy<3, true>, g, 256, st, lat, sweep, *m);
+    else e = launch_pdl(k_bonds_xy<3, false>, g, 256, st, lat, sweep, none);
   }
   if (blocks) *blocks = (int)g;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace swgb
