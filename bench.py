@@ -454,6 +454,10 @@ def run_batch(args):
         sw.sw_set_stream(h, st.cuda_stream)
         sw.sw_batch_add(b, h)
     sw.sw_batch_sweep(b, max(args.warmup, 3))
+    # untimed: every tile shape and label schedule on real sweeps of the batch
+    tune_ms = sw.sw_batch_autotune(b, 5)
+    cfg = sw.sw_batch_get_config(b)
+    sw.sw_batch_sweep(b, 1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(0)
@@ -486,11 +490,16 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": "ragged batch: 256 2D lattices, model uniform over Ising / Potts q=3 "
                                    "/ Potts q=4, L uniform over {32,48,...,1024}, T in [0.8,1.2] Tc, "
-                                   "seed 1003, one measured sweep per step, CUDA-graph replay",
+                                   "seed 1003, one measured sweep per step, CUDA-graph replay, "
+                                   "autotuned tile shape and label schedule",
                        "sites": sites, "l2": "inputs larger than L2"},
             "serial": {"value": v_serial, "unit": UNIT, "steps": k_serial,
                        "note": "each lattice alone with sw_sweep, one after another"},
             "speedup_vs_serial": v_batch / v_serial,
+            "autotune": {"chosen": cfg, "ms_per_sweep": {f"shape{sh}_schedule{sc}": round(float(tune_ms[sh, sc]), 4)
+                                                         for sh in range(tune_ms.shape[0])
+                                                         for sc in range(tune_ms.shape[1]) if tune_ms[sh, sc] > 0},
+                         "note": "5 timed sweeps per configuration, before the timed region"},
             # per step: labels of the Ising tiles and of the Potts tiles,
             # merge, compression, apply, step counter
             "gpu_launches": 6 * args.steps, "clocks": clk}

@@ -260,7 +260,36 @@ size_t sw_series_capacity(void);
  *                          member removes it from its batch first.
  * sw_device_bytes          device bytes sw_create would allocate for a lattice
  *                          (0 for invalid arguments): the budget a serving
- *                          loop admits jobs against. */
+ *                          loop admits jobs against.
+ *
+ * Launch configuration.  A batch's tiles are 32 x tile_y (x tile_z) sites,
+ * one CTA (a thread per 32-site row word) per tile, in one of
+ * SW_BATCH_TILE_SHAPES shapes: 2D 32x256, 32x128, 32x64; 3D 32x16x16,
+ * 32x16x8, 32x8x8 (shape 0 is the single-lattice tile).  The label schedule
+ * is 0 (the Ising tiles in one launch with the two-state layout, the Potts
+ * tiles in another) or 1 (all tiles in one launch, the Potts layout).  No
+ * configuration changes any result: bonds, draws and canonical labels are
+ * keyed by row word and site index, not by tile.
+ * sw_batch_set_config(b, shape, schedule)   selects one (SW_ERR_BAD_ARG out
+ *                          of range); the next sweep recaptures the graph.
+ * sw_batch_get_config(b, &shape, &schedule, &tile_y, &tile_z)   the current
+ *                          one (any pointer may be NULL; tile_z = 1 in 2D).
+ * sw_batch_autotune(b, sweeps, ms)   times every configuration on the
+ *                          batch itself and keeps the fastest: per
+ *                          configuration one untimed sweep (graph capture and
+ *                          upload), then `sweeps` sweeps timed with CUDA
+ *                          events (a host wait).  These are real measured
+ *                          sweeps of every member, as sw_batch_sweep's: with
+ *                          C = 3 shapes x (2 schedules if the batch holds both
+ *                          Ising and Potts lattices, else 1), every counter
+ *                          advances by C * (sweeps + 1).  ms (NULL or
+ *                          SW_BATCH_TILE_SHAPES * SW_BATCH_LABEL_SCHEDULES
+ *                          floats, index shape * 2 + schedule) receives the
+ *                          time per sweep of each configuration, -1 where not
+ *                          tried.  An empty batch returns SW_OK untouched;
+ *                          sweeps < 1 is SW_ERR_BAD_ARG. */
+#define SW_BATCH_TILE_SHAPES 3
+#define SW_BATCH_LABEL_SCHEDULES 2
 typedef struct sw_batch sw_batch;
 sw_batch* sw_batch_create(int dim);
 void sw_batch_destroy(sw_batch* b);
@@ -270,6 +299,9 @@ int sw_batch_sweep(sw_batch* b, int n);
 int sw_batch_set_stream(sw_batch* b, void* stream);
 size_t sw_batch_size(sw_batch* b);
 size_t sw_device_bytes(int model, int dim, int L, int q);
+int sw_batch_set_config(sw_batch* b, int shape, int schedule);
+int sw_batch_get_config(const sw_batch* b, int* shape, int* schedule, int* tile_y, int* tile_z);
+int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep);
 
 /* ------------------------------------------------------------------------
  * Asynchronous host I/O.  The paper has no counterpart (it times sweeps on a

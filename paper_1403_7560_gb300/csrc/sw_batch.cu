@@ -20,6 +20,9 @@
 using swgb::BatchMember;
 using swgb::BatchView;
 
+static_assert(SW_BATCH_TILE_SHAPES == swgb::kTileShapes && SW_BATCH_LABEL_SCHEDULES == swgb::kLabelSchedules,
+              "configuration counts of the public header");
+
 struct sw_batch {
   int dim = 0;
   cudaStream_t stream = nullptr;
@@ -34,6 +37,8 @@ struct sw_batch {
   uint32_t* d_step = nullptr;
   uint32_t ntiles = 0;
   uint32_t ising_tiles = 0;           // the tile map lists the Ising members' tiles first
+  int shape = 0;                      // tile shape (index into the shape table)
+  int schedule = 0;                   // label schedule (separate or one launch)
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev = nullptr;
 };
@@ -63,10 +68,25 @@ BatchView view(const sw_batch* b) {
   return v;
 }
 
-// Rebuild the tile map and the captured sweep after a membership change.
+// A member's lattice view in the batch's tile shape (tile counts and the
+// capacity of a tile's hooked list; the buffers hold the largest shape).
+swgb::Lattice member_view(const sw_batch* b, const sw_handle* h) {
+  swgb::Lattice lat = h->lat;
+  swgb::tiles_for(b->dim, h->L, &lat.ntx, &lat.nty, &lat.ntz, b->shape);
+  lat.hook_cap = swgb::merge_list_capacity(b->dim, b->shape);
+  return lat;
+}
+
+size_t member_tiles(const sw_batch* b, const sw_handle* h) {
+  const swgb::Lattice lat = member_view(b, h);
+  return (size_t)lat.ntx * lat.nty * lat.ntz;
+}
+
+// Rebuild the tile map and the captured sweep after a change of membership
+// or configuration.
 int rebuild(sw_batch* b) {
   size_t ntiles = 0;
-  for (sw_handle* h : b->members) ntiles += (size_t)h->lat.ntx * h->lat.nty * h->lat.ntz;
+  for (sw_handle* h : b->members) ntiles += member_tiles(b, h);
   if (ntiles > 0x7fffffffu) return bfail(SW_ERR_BAD_ARG, "batch has too many tiles");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch sync");
@@ -95,7 +115,7 @@ int rebuild(sw_batch* b) {
     for (size_t m = 0; m < b->members.size(); ++m) {
       const sw_handle* h = b->members[m];
       if ((h->model == SW_POTTS) != (pass == 1)) continue;
-      const uint32_t n = (uint32_t)((size_t)h->lat.ntx * h->lat.nty * h->lat.ntz);
+      const uint32_t n = (uint32_t)member_tiles(b, h);
       for (uint32_t k = 0; k < n; ++k, ++t) {
         lat[t] = (uint32_t)m;
         idx[t] = k;
@@ -116,9 +136,10 @@ int rebuild(sw_batch* b) {
     const BatchView v = view(b);
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t le = swgb::launch_label_batch(v, b->dim, b->ising_tiles, b->ntiles - b->ising_tiles, b->stream);
-      if (le == cudaSuccess) le = swgb::launch_merge_batch(v, b->dim, b->ntiles, b->stream);
-      if (le == cudaSuccess) le = swgb::launch_flip_batch(v, b->dim, b->ntiles, b->stream);
+      cudaError_t le = swgb::launch_label_batch(v, b->dim, b->shape, b->schedule, b->ising_tiles,
+                                                b->ntiles - b->ising_tiles, b->stream);
+      if (le == cudaSuccess) le = swgb::launch_merge_batch(v, b->dim, b->shape, b->ntiles, b->stream);
+      if (le == cudaSuccess) le = swgb::launch_flip_batch(v, b->dim, b->shape, b->ntiles, b->stream);
       e = cudaStreamEndCapture(b->stream, &g);
       if (e == cudaSuccess) e = le;
     }
@@ -217,7 +238,13 @@ int sw_batch_set_stream(sw_batch* b, void* stream) {
   return SW_OK;
 }
 
-int sw_batch_sweep(sw_batch* b, int n) {
+}  // extern "C"
+
+namespace {
+
+// n sweeps of every member (graph replays); with ms != nullptr the replays
+// alone are timed with events on the batch stream (a host wait).
+int batch_sweep(sw_batch* b, int n, float* ms) {
   if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
   if (n < 0) return bfail(SW_ERR_BAD_ARG, "n < 0");
   if (n == 0 || b->members.empty()) return SW_OK;
@@ -237,7 +264,7 @@ int sw_batch_sweep(sw_batch* b, int n) {
   if (e != cudaSuccess) return bcuda(e, "batch ordering");
   for (size_t m = 0; m < b->members.size(); ++m) {
     const sw_handle* h = b->members[m];
-    b->h_members[m].lat = h->lat;
+    b->h_members[m].lat = member_view(b, h);
     b->h_members[m].meas = h->meas;
     b->h_members[m].sweep0 = (uint32_t)h->sweep;
   }
@@ -245,16 +272,94 @@ int sw_batch_sweep(sw_batch* b, int n) {
                            cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(b->d_step, 0, sizeof(uint32_t), b->stream)) != cudaSuccess)
     return bcuda(e, "batch descriptors");
-  for (int s = 0; s < n; ++s)
-    if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return bcuda(e, "batch sweep");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (ms) {
+    if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess ||
+        (e = cudaEventRecord(t0, b->stream)) != cudaSuccess) {
+      if (t0) cudaEventDestroy(t0);
+      return bcuda(e, "batch timing");
+    }
+  }
+  for (int s = 0; s < n && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->graph, b->stream);
+  if (e == cudaSuccess && ms) e = cudaEventRecord(t1, b->stream);
   // later work on each member waits for the batch
-  if ((e = cudaEventRecord(b->ev, b->stream)) != cudaSuccess) return bcuda(e, "batch event");
-  for (sw_handle* h : b->members) {
-    if ((e = cudaStreamWaitEvent(h->stream, b->ev, 0)) != cudaSuccess) return bcuda(e, "batch event");
-    h->sweep += (uint64_t)n;
-    h->pending = h->sweep;  // the last sweep's record, written on demand
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->stream);
+  if (e == cudaSuccess) {
+    for (sw_handle* h : b->members) {
+      if ((e = cudaStreamWaitEvent(h->stream, b->ev, 0)) != cudaSuccess) break;
+      h->sweep += (uint64_t)n;
+      h->pending = h->sweep;  // the last sweep's record, written on demand
+    }
+  }
+  if (e == cudaSuccess && ms) e = cudaEventSynchronize(t1);
+  if (e == cudaSuccess && ms) e = cudaEventElapsedTime(ms, t0, t1);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  return e == cudaSuccess ? SW_OK : bcuda(e, "batch sweep");
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_batch_sweep(sw_batch* b, int n) { return batch_sweep(b, n, nullptr); }
+
+int sw_batch_set_config(sw_batch* b, int shape, int schedule) {
+  if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
+  if (shape < 0 || shape >= swgb::kTileShapes) return bfail(SW_ERR_BAD_ARG, "tile shape out of range");
+  if (schedule < 0 || schedule >= swgb::kLabelSchedules) return bfail(SW_ERR_BAD_ARG, "label schedule out of range");
+  if (shape != b->shape || schedule != b->schedule) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);  // the replays in flight use the old tile map
+    if (e != cudaSuccess) return bcuda(e, "batch sync");
+    b->shape = shape;
+    b->schedule = schedule;
+    b->dirty = true;
   }
   return SW_OK;
+}
+
+int sw_batch_get_config(const sw_batch* b, int* shape, int* schedule, int* tile_y, int* tile_z) {
+  if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
+  if (shape) *shape = b->shape;
+  if (schedule) *schedule = b->schedule;
+  if (tile_y) *tile_y = swgb::kShapeTY[b->dim - 2][b->shape];
+  if (tile_z) *tile_z = swgb::kShapeTZ[b->dim - 2][b->shape];
+  return SW_OK;
+}
+
+int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep) {
+  if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
+  if (sweeps < 1) return bfail(SW_ERR_BAD_ARG, "sweeps < 1");
+  constexpr int kConfigs = swgb::kTileShapes * swgb::kLabelSchedules;
+  if (ms_per_sweep)
+    for (int c = 0; c < kConfigs; ++c) ms_per_sweep[c] = -1.0f;
+  if (b->members.empty()) return SW_OK;
+  bool ising = false, potts = false;
+  for (const sw_handle* h : b->members) (h->model == SW_POTTS ? potts : ising) = true;
+  // one label launch differs from two only when both kinds are present
+  const int schedules = (ising && potts) ? swgb::kLabelSchedules : 1;
+  const uint64_t total = (uint64_t)swgb::kTileShapes * schedules * ((uint64_t)sweeps + 1);
+  for (const sw_handle* h : b->members)
+    if (h->sweep + total >= 0xffffffffull) return bfail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+  int best_shape = b->shape, best_schedule = b->schedule;
+  float best = -1.0f;
+  for (int sh = 0; sh < swgb::kTileShapes; ++sh) {
+    for (int sc = 0; sc < schedules; ++sc) {
+      int rc = sw_batch_set_config(b, sh, sc);
+      if (rc == SW_OK) rc = batch_sweep(b, 1, nullptr);  // graph capture and upload, untimed
+      float ms = 0.0f;
+      if (rc == SW_OK) rc = batch_sweep(b, sweeps, &ms);
+      if (rc != SW_OK) return rc;
+      ms /= (float)sweeps;
+      if (ms_per_sweep) ms_per_sweep[sh * swgb::kLabelSchedules + sc] = ms;
+      if (best < 0.0f || ms < best) {
+        best = ms;
+        best_shape = sh;
+        best_schedule = sc;
+      }
+    }
+  }
+  return sw_batch_set_config(b, best_shape, best_schedule);
 }
 
 size_t sw_device_bytes(int model, int dim, int L, int q) {
@@ -262,15 +367,13 @@ size_t sw_device_bytes(int model, int dim, int L, int q) {
   double n = 1.0;
   for (int d = 0; d < dim; ++d) n *= L;
   if (n > 4294967295.0) return 0;
-  int ntx, nty, ntz;
-  swgb::tiles_for(dim, L, &ntx, &nty, &ntz);
   const size_t N = (size_t)n;
   const size_t words = (size_t)dim * (N / (size_t)L) * (size_t)((L + 31) / 32);
-  const size_t ntiles = (size_t)ntx * nty * ntz;
+  size_t ntiles = 0, hook_words = 0;
+  swgb::tile_buffers(model, dim, L, &ntiles, &hook_words);
   const size_t spins = N * (model == SW_XY ? 4 : model == SW_CLOCK ? 2 : 1);
   const size_t clock = (model == SW_CLOCK) ? (size_t)4 * q * q * 4 + (size_t)2 * q * 8 + 3 * swgb::kSlots * 8 : 0;
-  return spins + 4 * words + 4 * N + ntiles * (size_t)swgb::merge_list_capacity(dim) * 4 + ntiles * 4 +
-         swgb::handle_block_bytes() + clock;
+  return spins + 4 * words + 4 * N + hook_words * 4 + ntiles * 4 + swgb::handle_block_bytes() + clock;
 }
 
 }  // extern "C"

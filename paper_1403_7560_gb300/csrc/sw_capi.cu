@@ -275,8 +275,9 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   swgb::set_philox_key(lat, seed);
   lat.model = model;
   h->bond_words = (size_t)dim * lat.R * (size_t)lat.W;
-  const size_t ntiles = (size_t)lat.ntx * lat.nty * lat.ntz;
   lat.hook_cap = swgb::merge_list_capacity(dim);
+  size_t tile_bufs = 0, hook_words = 0;  // sized for every tile shape a batch may use
+  swgb::tile_buffers(model, dim, L, &tile_bufs, &hook_words);
 
   cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { cuda_fail(e, "stream"); release(h); return nullptr; }
@@ -291,8 +292,8 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   if ((e = cudaMalloc(&lat.spins, h->spin_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&lat.planes, h->bond_words * 4)) != cudaSuccess ||
       (e = cudaMalloc(&lat.forest, (size_t)N * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&lat.hooked, ntiles * (size_t)lat.hook_cap * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&lat.nhooked, ntiles * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&lat.hooked, hook_words * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&lat.nhooked, tile_bufs * 4)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_block, block_bytes)) != cudaSuccess) {
     fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,
          std::string("device allocation: ") + cudaGetErrorString(e));

@@ -135,32 +135,32 @@ __device__ __forceinline__ uint32_t run_start(uint32_t starts, int b) {
 }
 
 // ---------------------------------------------------------------- tiles
-// A tile is 32 (one bit-plane word) x TY x TZ sites; one CTA of TY*TZ
-// threads labels it.
+// A tile is 32 (one bit-plane word) x TY x TZ sites; one CTA of
+// THREADS = TY*TZ threads (a thread per row word) labels it.  Shape S of
+// dimension D is the S-th entry of the shape table; Tile<D> is shape 0,
+// the single-lattice tile.
+template <int D_, int TY_, int TZ_>
+struct TileShape {
+  static constexpr int D = D_, TY = TY_, TZ = TZ_, ROWS = TY_ * TZ_, THREADS = TY_ * TZ_;
+};
+template <int D, int S>
+using ShapeOf = TileShape<D, kShapeTY[D - 2][S], kShapeTZ[D - 2][S]>;
 template <int D>
-struct Tile;
-template <>
-struct Tile<2> {
-  static constexpr int TY = kTile2Y, TZ = 1, ROWS = TY * TZ;
-};
-template <>
-struct Tile<3> {
-  static constexpr int TY = kTile3Y, TZ = kTile3Z, ROWS = TY * TZ;
-};
+using Tile = ShapeOf<D, 0>;
 
 struct TileCoord {
   int tx, x0, y0, z0;
 };
 
-template <int D>
+template <class S>
 __device__ __forceinline__ TileCoord tile_coord(const Lattice& lat, uint32_t tile) {
   int b = (int)tile;
   TileCoord c;
   c.tx = b % lat.ntx;
   b /= lat.ntx;
   c.x0 = c.tx * 32;
-  c.y0 = (b % lat.nty) * Tile<D>::TY;
-  c.z0 = (b / lat.nty) * Tile<D>::TZ;
+  c.y0 = (b % lat.nty) * S::TY;
+  c.z0 = (b / lat.nty) * S::TZ;
   return c;
 }
 

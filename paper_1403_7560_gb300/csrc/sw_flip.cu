@@ -18,6 +18,8 @@
 //   its new state (set at random for Ising/Potts, reflection about the
 //   mirror line for XY); global roots are counted.
 // k_labels_out: canonical labels (walk to the root) for readout.
+#include <algorithm>
+
 #include "sw_device.cuh"
 
 namespace swgb {
@@ -25,26 +27,26 @@ namespace {
 
 using namespace dev;
 
-template <int D>
+template <class S>
 struct MergeShape {
   // face bonds a tile owns: +x face, +y face (and +z face)
-  static constexpr int kMax = Tile<D>::ROWS + 32 * Tile<D>::TZ + (D == 3 ? 32 * Tile<D>::TY : 0);
-  static constexpr int kPerThread = (kMax + kTileThreads - 1) / kTileThreads;
+  static constexpr int kMax = S::ROWS + 32 * S::TZ + (S::D == 3 ? 32 * S::TY : 0);
+  static constexpr int kPerThread = (kMax + S::THREADS - 1) / S::THREADS;
 };
 
-template <int D>
+template <class S>
 struct MergeSmem {
-  uint2 list[MergeShape<D>::kMax];
+  uint2 list[MergeShape<S>::kMax];
   int n;
 };
 
-template <int D>
-__device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, MergeSmem<D>& sm) {
-  constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  constexpr int NC = MergeShape<D>::kPerThread;
+template <class S>
+__device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, MergeSmem<S>& sm) {
+  constexpr int D = S::D, TY = S::TY, TZ = S::TZ, NT = S::THREADS;
+  constexpr int NC = MergeShape<S>::kPerThread;
   uint2* s_list = sm.list;
   int& s_n = sm.n;
-  const TileCoord tc = tile_coord<D>(lat, tile);
+  const TileCoord tc = tile_coord<S>(lat, tile);
   const int L = lat.L;
   const int shift = lat.sbits + 1;
   const int nx = min(32, L - tc.x0), ny = min(TY, L - tc.y0), nz = (D == 3) ? min(TZ, L - tc.z0) : 1;
@@ -62,7 +64,7 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   bool on[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    const int c = threadIdx.x + k * kTileThreads;
+    const int c = threadIdx.x + k * NT;
     on[k] = false;
     ii[k] = jj[k] = 0u;
     if (c >= total) continue;
@@ -108,7 +110,7 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   // every root this tile hooks goes to the tile's hooked list for k_compress
   // (no list on the labeling-only paths)
   uint32_t* hooked = lat.hooked ? lat.hooked + (size_t)tile * (size_t)lat.hook_cap : nullptr;
-  for (int e = threadIdx.x; e < n; e += kTileThreads) {
+  for (int e = threadIdx.x; e < n; e += NT) {
     const uint32_t h = gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err);
     if (hooked && h != 0xffffffffu) hooked[atomicAdd(&s_n, 1)] = h;
   }
@@ -118,16 +120,19 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
 
 template <int D>
 __global__ void __launch_bounds__(kTileThreads, 8) k_merge(Lattice lat) {
-  __shared__ MergeSmem<D> sm;
-  merge_tile<D>(lat, blockIdx.x, sm);
+  __shared__ MergeSmem<Tile<D>> sm;
+  merge_tile<Tile<D>>(lat, blockIdx.x, sm);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kTileThreads, 8) k_merge_batch(BatchView bv) {
-  __shared__ MergeSmem<D> sm;
+// Eight 256-thread CTAs per SM, proportionally more of smaller tiles.
+constexpr int merge_blocks(int threads) { return 8 * 256 / threads > 32 ? 32 : 8 * 256 / threads; }
+
+template <class S>
+__global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_batch(BatchView bv) {
+  __shared__ MergeSmem<S> sm;
   pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
-  merge_tile<D>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
+  merge_tile<S>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
 }
 
 constexpr int kFlipThreads = 256, kFlipWarps = kFlipThreads / 32;
@@ -252,17 +257,18 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
 
 // Batch apply: one CTA per member tile, warps over the tile's rows, lanes
 // over x; the member's model picks the state update.
-template <int D>
+template <class S>
 __global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
-  constexpr int TY = Tile<D>::TY, ROWS = Tile<D>::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
+  constexpr int D = S::D, TY = S::TY, ROWS = S::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
   constexpr int B = 8;
+  static_assert(RPW % B == 0, "whole batches of rows per warp");
   __shared__ long long s_red[NW];
   pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   const Lattice& lat = m.lat;
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const uint32_t sweep = m.sweep0 + *bv.step + 1u;
-  const TileCoord tc = tile_coord<D>(lat, tile);
+  const TileCoord tc = tile_coord<S>(lat, tile);
   const int L = lat.L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sb = lat.sbits, shift = sb + 1;
   const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
@@ -320,7 +326,30 @@ __global__ void __launch_bounds__(256) k_labels_out(Lattice lat, int32_t* out) {
 
 }  // namespace
 
-int merge_list_capacity(int dim) { return dim == 2 ? MergeShape<2>::kMax : MergeShape<3>::kMax; }
+namespace {
+template <int D>
+int merge_capacity_dim(int shape) {
+  if (shape == 1) return MergeShape<ShapeOf<D, 1>>::kMax;
+  if (shape == 2) return MergeShape<ShapeOf<D, 2>>::kMax;
+  return MergeShape<ShapeOf<D, 0>>::kMax;
+}
+}  // namespace
+
+int merge_list_capacity(int dim, int shape) {
+  return dim == 2 ? merge_capacity_dim<2>(shape) : merge_capacity_dim<3>(shape);
+}
+
+void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words) {
+  const bool batchable = model == kIsing || model == kPotts;
+  *ntiles = *hook_words = 0;
+  for (int s = 0; s < (batchable ? kTileShapes : 1); ++s) {
+    int ntx, nty, ntz;
+    tiles_for(dim, L, &ntx, &nty, &ntz, s);
+    const size_t n = (size_t)ntx * nty * ntz;
+    *ntiles = std::max(*ntiles, n);
+    *hook_words = std::max(*hook_words, n * (size_t)merge_list_capacity(dim, s));
+  }
+}
 
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
@@ -342,18 +371,45 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
   return launch_pdl(k_apply<kXY>, g, kFlipThreads, st, lat, sweep, m, count);
 }
 
-cudaError_t launch_merge_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
-  if (dim == 2) return launch_pdl(k_merge_batch<2>, ntiles, kTileThreads, st, bv);
-  return launch_pdl(k_merge_batch<3>, ntiles, kTileThreads, st, bv);
+namespace {
+
+template <int D, int SH>
+cudaError_t merge_batch_shape(const BatchView& bv, uint32_t ntiles, cudaStream_t st) {
+  using S = ShapeOf<D, SH>;
+  return launch_pdl(k_merge_batch<S>, ntiles, (unsigned)S::THREADS, st, bv);
 }
 
-cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st) {
+template <int D, int SH>
+cudaError_t flip_batch_shape(const BatchView& bv, uint32_t ntiles, cudaStream_t st) {
   cudaError_t e = launch_pdl(k_compress_batch, ntiles, kFlipThreads, st, bv);
-  if (e == cudaSuccess)
-    e = (dim == 2) ? launch_pdl(k_apply_batch<2>, ntiles, kFlipThreads, st, bv)
-                   : launch_pdl(k_apply_batch<3>, ntiles, kFlipThreads, st, bv);
+  if (e == cudaSuccess) e = launch_pdl(k_apply_batch<ShapeOf<D, SH>>, ntiles, kFlipThreads, st, bv);
   if (e == cudaSuccess) e = launch_pdl(k_advance, 1u, 1u, st, bv.step);
   return e;
+}
+
+template <int D>
+cudaError_t merge_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, cudaStream_t st) {
+  if (shape == 1) return merge_batch_shape<D, 1>(bv, ntiles, st);
+  if (shape == 2) return merge_batch_shape<D, 2>(bv, ntiles, st);
+  return merge_batch_shape<D, 0>(bv, ntiles, st);
+}
+
+template <int D>
+cudaError_t flip_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, cudaStream_t st) {
+  if (shape == 1) return flip_batch_shape<D, 1>(bv, ntiles, st);
+  if (shape == 2) return flip_batch_shape<D, 2>(bv, ntiles, st);
+  return flip_batch_shape<D, 0>(bv, ntiles, st);
+}
+
+}  // namespace
+
+cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st) {
+  static_assert(kTileShapes == 3, "one instantiation per shape");
+  return dim == 2 ? merge_batch_dim<2>(bv, shape, ntiles, st) : merge_batch_dim<3>(bv, shape, ntiles, st);
+}
+
+cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st) {
+  return dim == 2 ? flip_batch_dim<2>(bv, shape, ntiles, st) : flip_batch_dim<3>(bv, shape, ntiles, st);
 }
 
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st) {

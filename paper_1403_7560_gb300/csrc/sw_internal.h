@@ -95,12 +95,16 @@ struct Record {
 constexpr int kMeasureBlocks = 1216;  // 152 SMs x 8 blocks of 256 threads
 constexpr int kMaxClockQ = 1024;      // largest q of the clock model
 
-// Tile shape of the labeling, merge and flip kernels: 32 sites along x (one
-// bit-plane word) by TY (by TZ); one CTA of TY*TZ threads per tile.
-constexpr int kTile2Y = 256;  // 2D: 32 x 256 sites
-constexpr int kTile3Y = 16;   // 3D: 32 x 16 x 16 sites
-constexpr int kTile3Z = 16;
-constexpr int kTileThreads = 256;
+// Tile shapes of the labeling and merge kernels: 32 sites along x (one
+// bit-plane word) by TY (by TZ); one CTA of TY*TZ threads (a thread per row
+// word) per tile.  Shape 0 of each dimension is the one single lattices
+// use; a batch runs any of them (sw_batch_autotune times them).  A tile's
+// shape changes no result: bond words, draws and canonical roots are keyed
+// by row word and site index only.
+constexpr int kTileShapes = 3;
+constexpr int kShapeTY[2][kTileShapes] = {{256, 128, 64}, {16, 16, 8}};
+constexpr int kShapeTZ[2][kTileShapes] = {{1, 1, 1}, {16, 8, 8}};
+constexpr int kTileThreads = 256;  // threads of a shape-0 tile (2D and 3D)
 
 // Launches kernel k with programmatic stream serialisation: its launch is
 // processed while the preceding kernel in the stream runs, and it waits for
@@ -122,10 +126,15 @@ cudaError_t launch_pdl(void (*k)(K...), unsigned grid, unsigned block, cudaStrea
   return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
 }
 
-void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz);
+// Tiles per axis of an L^dim lattice in tile shape `shape` (default 0).
+void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz, int shape = 0);
 // Bonds that leave one tile (its +x, +y, +z faces): the most roots one
 // tile's merge can hook.
-int merge_list_capacity(int dim);
+int merge_list_capacity(int dim, int shape = 0);
+// Sizes of a lattice's per-tile buffers (the hooked-root counters and
+// lists): for Ising/Potts lattices, which may join a batch, the largest
+// over all tile shapes; for the others, shape 0's.
+void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words);
 
 // Message returned by sw_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
@@ -160,13 +169,16 @@ cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const 
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);
 
 // Batched phases: one launch over every tile of every member (Ising/Potts,
-// one dimension), then the step counter advances.
+// one dimension, tile shape `shape`), then the step counter advances.
 // The tile map lists the Ising members' tiles first (ising_tiles of them),
-// then the Potts members' tiles.
-cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ising_tiles, uint32_t potts_tiles,
-                               cudaStream_t st);
-cudaError_t launch_merge_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
-cudaError_t launch_flip_batch(const BatchView& bv, int dim, uint32_t ntiles, cudaStream_t st);
+// then the Potts members' tiles.  Label schedule 0: the Ising tiles in one
+// launch (two-state layout), the Potts tiles in another; schedule 1: every
+// tile in one launch (Potts layout, the member's model picked per tile).
+constexpr int kLabelSchedules = 2;
+cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ising_tiles,
+                               uint32_t potts_tiles, cudaStream_t st);
+cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st);
+cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st);
 
 // Write the record of a pending measured sweep of h (stand-alone kernel).
 cudaError_t flush_pending(struct ::sw_handle* h);

@@ -88,9 +88,9 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
 // kernel of this sweep writes the record of sweep - 1).  MM = 0: none.
 // Shared memory of one tile's labeling in measurement mode MM (the Potts
 // draw words and histograms only where Potts lattices can run).
-template <int D, int MM>
+template <class S, int MM>
 struct LabelSmem {
-  static constexpr int ROWS = Tile<D>::ROWS, NW = kTileThreads / 32;
+  static constexpr int ROWS = S::ROWS, NW = S::THREADS / 32;
   static constexpr bool kPottsDraws = MM != 1;  // MM 1: Ising only (two-state draws)
   static constexpr int kDrawWords = (kPottsDraws ? 8 : 1) * (ROWS + 1);
   static constexpr int kHist = MM == 2 ? 256 : 1, kWHist = MM == 2 ? NW * kSmallQ : 1;
@@ -107,13 +107,13 @@ struct LabelSmem {
   long long s_red[NW];
 };
 
-template <int D, bool FROM_MASK, int MM, class Smem>
+template <class Sh, bool FROM_MASK, int MM, class Smem>
 __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, uint32_t sweep,
                                            const Measure& mb, Smem& sm) {
   constexpr bool MEASURE = MM != 0;
-  constexpr int TY = Tile<D>::TY, TZ = Tile<D>::TZ, ROWS = Tile<D>::ROWS;
-  constexpr int NW = kTileThreads / 32, RPW = ROWS / NW;
-  static_assert(ROWS == kTileThreads, "one thread per row word");
+  constexpr int D = Sh::D, TY = Sh::TY, TZ = Sh::TZ, ROWS = Sh::ROWS, NT = Sh::THREADS;
+  constexpr int NW = NT / 32, RPW = ROWS / NW;
+  static_assert(ROWS == NT && NT % 32 == 0, "one thread per row word, whole warps");
   static_assert(!(MEASURE && FROM_MASK), "measurement needs the spins");
   uint32_t* par = sm.par;
   uint32_t* sdraw = sm.sdraw;
@@ -124,12 +124,12 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   long long* s_red = sm.s_red;
   int m_acc = 0, e_acc = 0;
   if (MM == 2) {
-    for (int k = threadIdx.x; k < 256; k += kTileThreads) s_hist[k] = 0u;
-    for (int k = threadIdx.x; k < NW * kSmallQ; k += kTileThreads) s_whist[k] = 0u;
+    for (int k = threadIdx.x; k < 256; k += NT) s_hist[k] = 0u;
+    for (int k = threadIdx.x; k < NW * kSmallQ; k += NT) s_whist[k] = 0u;
     __syncthreads();
   }
 
-  const TileCoord tc = tile_coord<D>(lat, tile);
+  const TileCoord tc = tile_coord<Sh>(lat, tile);
   const int L = lat.L;
   const uint32_t plane = lat.R * (uint32_t)lat.W;
   const int nvalid = min(32, L - tc.x0);
@@ -143,9 +143,9 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   {
     uint4* p4 = reinterpret_cast<uint4*>(par);
 #pragma unroll
-    for (int k = 0; k < ROWS * 32 / 4 / kTileThreads; ++k) {
-      const uint32_t t = 4u * (uint32_t)(threadIdx.x + k * kTileThreads);
-      p4[threadIdx.x + k * kTileThreads] = make_uint4(t, t + 1u, t + 2u, t + 3u);
+    for (int k = 0; k < ROWS * 32 / 4 / NT; ++k) {
+      const uint32_t t = 4u * (uint32_t)(threadIdx.x + k * NT);
+      p4[threadIdx.x + k * NT] = make_uint4(t, t + 1u, t + 2u, t + 3u);
     }
   }
 
@@ -295,7 +295,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   if (MEASURE) {
     if (MM == 2) {
       __syncthreads();
-      for (int k = threadIdx.x; k < kSmallQ; k += kTileThreads)
+      for (int k = threadIdx.x; k < kSmallQ; k += NT)
         for (int w = 0; w < NW; ++w) s_hist[k] += s_whist[w * kSmallQ + k];
       __syncthreads();
       add_histogram(lat, mb, tile, s_hist);
@@ -307,33 +307,44 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
 template <int D, bool FROM_MASK, int MM>
 __global__ void __launch_bounds__(kTileThreads, 5) k_label(const __grid_constant__ Lattice lat, uint32_t sweep,
                                                               const __grid_constant__ Measure mb) {
-  __shared__ LabelSmem<D, MM> sm;
-  label_tile<D, FROM_MASK, MM>(lat, blockIdx.x, sweep, mb, sm);
+  static_assert(Tile<D>::THREADS == kTileThreads, "shape-0 tiles");
+  __shared__ LabelSmem<Tile<D>, MM> sm;
+  label_tile<Tile<D>, FROM_MASK, MM>(lat, blockIdx.x, sweep, mb, sm);
 }
 
-// Ising/Potts lattices of a batch, one tile per CTA; sweep numbers come from
-// the batch step counter, and every step after the first also measures the
-// incoming state of its lattice (the record of the previous sweep).  The
-// tile map lists the Ising members' tiles first: they run in one launch
-// with the two-state layout (five CTAs per SM), the Potts tiles in another.
-template <int D, bool POTTS>
-__global__ void __launch_bounds__(kTileThreads, POTTS ? 4 : 5) k_label_batch(BatchView bv, uint32_t first) {
-  __shared__ LabelSmem<D, POTTS ? 2 : 1> sm;
+// Ising/Potts lattices of a batch, one tile of shape S per CTA; sweep
+// numbers come from the batch step counter, and every step after the first
+// also measures the incoming state of its lattice (the record of the
+// previous sweep).  The tile map lists the Ising members' tiles first.
+// LAYOUT 1: Ising tiles only, two-state layout; LAYOUT 2: Potts tiles only;
+// LAYOUT 3: any tile, Potts layout, the member's model picked per tile.
+// Resident CTAs per SM: five 256-thread CTAs (two-state layout) or four
+// (Potts layout), and proportionally more of smaller tiles.
+constexpr int label_blocks(int threads, int layout) {
+  return (layout == 1 ? 5 : 4) * 256 / threads > 32 ? 32 : (layout == 1 ? 5 : 4) * 256 / threads;
+}
+
+template <class S, int LAYOUT>
+__global__ void __launch_bounds__(S::THREADS, label_blocks(S::THREADS, LAYOUT))
+    k_label_batch(BatchView bv, uint32_t first) {
+  __shared__ LabelSmem<S, LAYOUT == 1 ? 1 : 2> sm;
   // the member's lattice view is copied to shared memory: the Philox round
   // keys are read on every round
   __shared__ Lattice s_lat;
-  static_assert(sizeof(Lattice) % 4 == 0 && sizeof(Lattice) / 4 <= kTileThreads, "lattice copy");
+  static_assert(sizeof(Lattice) % 4 == 0, "lattice copy");
   pdl_wait();
   const uint32_t b = __ldg(&bv.tile_lattice[first + blockIdx.x]);
   const uint32_t tile = __ldg(&bv.tile_index[first + blockIdx.x]);
   const BatchMember& m = bv.members[b];
-  if (threadIdx.x < sizeof(Lattice) / 4)
-    reinterpret_cast<uint32_t*>(&s_lat)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&m.lat)[threadIdx.x];
+  for (uint32_t k = threadIdx.x; k < sizeof(Lattice) / 4; k += S::THREADS)
+    reinterpret_cast<uint32_t*>(&s_lat)[k] = reinterpret_cast<const uint32_t*>(&m.lat)[k];
   __syncthreads();
   const uint32_t step = *bv.step;
   const uint32_t sweep = m.sweep0 + step + 1u;
-  if (step == 0u) label_tile<D, false, 0>(s_lat, tile, sweep, m.meas, sm);
-  else label_tile<D, false, POTTS ? 2 : 1>(s_lat, tile, sweep, m.meas, sm);
+  const bool potts = LAYOUT == 2 || (LAYOUT == 3 && s_lat.model == kPotts);
+  if (step == 0u) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
+  else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
+  else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
 }
 
 // ---------------------------------------------------------------- XY bonds
@@ -545,15 +556,11 @@ cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, const Measure
   return e;
 }
 
-void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz) {
+void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz, int shape) {
+  const int ty = kShapeTY[dim - 2][shape], tz = kShapeTZ[dim - 2][shape];
   *ntx = (L + 31) / 32;
-  if (dim == 2) {
-    *nty = (L + kTile2Y - 1) / kTile2Y;
-    *ntz = 1;
-  } else {
-    *nty = (L + kTile3Y - 1) / kTile3Y;
-    *ntz = (L + kTile3Z - 1) / kTile3Z;
-  }
+  *nty = (L + ty - 1) / ty;
+  *ntz = (dim == 2) ? 1 : (L + tz - 1) / tz;
 }
 
 cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st) {
@@ -570,18 +577,36 @@ cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cud
   return e;
 }
 
-cudaError_t launch_label_batch(const BatchView& bv, int dim, uint32_t ising_tiles, uint32_t potts_tiles,
-                               cudaStream_t st) {
+namespace {
+
+template <int D, int SH>
+cudaError_t label_batch_shape(const BatchView& bv, int schedule, uint32_t ising_tiles, uint32_t potts_tiles,
+                              cudaStream_t st) {
+  using S = ShapeOf<D, SH>;
+  if (schedule == 1 && ising_tiles && potts_tiles)
+    return launch_pdl(k_label_batch<S, 3>, ising_tiles + potts_tiles, (unsigned)S::THREADS, st, bv, 0u);
   cudaError_t e = cudaSuccess;
-  if (ising_tiles) {
-    if (dim == 2) e = launch_pdl(k_label_batch<2, false>, ising_tiles, kTileThreads, st, bv, 0u);
-    else e = launch_pdl(k_label_batch<3, false>, ising_tiles, kTileThreads, st, bv, 0u);
-  }
-  if (e == cudaSuccess && potts_tiles) {
-    if (dim == 2) e = launch_pdl(k_label_batch<2, true>, potts_tiles, kTileThreads, st, bv, ising_tiles);
-    else e = launch_pdl(k_label_batch<3, true>, potts_tiles, kTileThreads, st, bv, ising_tiles);
-  }
+  if (ising_tiles) e = launch_pdl(k_label_batch<S, 1>, ising_tiles, (unsigned)S::THREADS, st, bv, 0u);
+  if (e == cudaSuccess && potts_tiles)
+    e = launch_pdl(k_label_batch<S, 2>, potts_tiles, (unsigned)S::THREADS, st, bv, ising_tiles);
   return e;
+}
+
+template <int D>
+cudaError_t label_batch_dim(const BatchView& bv, int shape, int schedule, uint32_t ising_tiles,
+                            uint32_t potts_tiles, cudaStream_t st) {
+  if (shape == 1) return label_batch_shape<D, 1>(bv, schedule, ising_tiles, potts_tiles, st);
+  if (shape == 2) return label_batch_shape<D, 2>(bv, schedule, ising_tiles, potts_tiles, st);
+  return label_batch_shape<D, 0>(bv, schedule, ising_tiles, potts_tiles, st);
+}
+
+}  // namespace
+
+cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ising_tiles,
+                               uint32_t potts_tiles, cudaStream_t st) {
+  static_assert(kTileShapes == 3, "one instantiation per shape");
+  if (dim == 2) return label_batch_dim<2>(bv, shape, schedule, ising_tiles, potts_tiles, st);
+  return label_batch_dim<3>(bv, shape, schedule, ising_tiles, potts_tiles, st);
 }
 
 cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Measure& m,

@@ -79,10 +79,15 @@ _SIGNATURES = {
     "sw_batch_set_stream": (_i, [_vp, _vp]),
     "sw_batch_size": (_sz, [_vp]),
     "sw_device_bytes": (_sz, [_i, _i, _i, _i]),
+    "sw_batch_set_config": (_i, [_vp, _i, _i]),
+    "sw_batch_get_config": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                 ctypes.POINTER(_i)]),
+    "sw_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_float)]),
 }
 
 SW_NOALLOC_MAX_SITES = 1 << 21
 SW_LABEL_TILE_UF, SW_LABEL_EQUIVALENCE = 0, 1
+SW_BATCH_TILE_SHAPES, SW_BATCH_LABEL_SCHEDULES = 3, 2
 
 
 def library_path() -> str:
@@ -342,6 +347,25 @@ def sw_batch_set_stream(b: Batch, stream: int):
 
 def sw_batch_size(b: Batch) -> int:
     return int(lib().sw_batch_size(b))
+
+
+def sw_batch_set_config(b: Batch, shape: int, schedule: int):
+    _check(lib().sw_batch_set_config(b, shape, schedule))
+
+
+def sw_batch_get_config(b: Batch) -> dict:
+    """The batch's tile shape index, label schedule and tile extents."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().sw_batch_get_config(b, *[ctypes.byref(x) for x in v]))
+    return {"shape": v[0].value, "schedule": v[1].value, "tile_y": v[2].value, "tile_z": v[3].value}
+
+
+def sw_batch_autotune(b: Batch, sweeps: int) -> np.ndarray:
+    """Times every (shape, schedule) on real sweeps of the batch and keeps the
+    fastest; returns ms per sweep as [shape, schedule] (-1 where not tried)."""
+    ms = (ctypes.c_float * (SW_BATCH_TILE_SHAPES * SW_BATCH_LABEL_SCHEDULES))()
+    _check(lib().sw_batch_autotune(b, sweeps, ms))
+    return np.array(list(ms), dtype=np.float64).reshape(SW_BATCH_TILE_SHAPES, SW_BATCH_LABEL_SCHEDULES)
 
 
 def sw_device_bytes(model: int, dim: int, L: int, q: int) -> int:

@@ -70,6 +70,9 @@ def test_null_handle_calls_fail_cleanly(swlib):
     assert lib.sw_get_spins_async(None, None, 0) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_get_record_async(None, 1, None) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_wait_io(None) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_batch_set_config(None, 0, 0) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_batch_get_config(None, None, None, None, None) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_batch_autotune(None, 1, None) == swlib.SW_ERR_BAD_ARG
     lib.sw_destroy(None)
     assert swlib.sw_series_capacity() >= 1024
 

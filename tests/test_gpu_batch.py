@@ -138,3 +138,87 @@ def test_batch_rules(sw):
         for h in (xy, d3, ok):
             if h is not None:
                 sw.sw_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("specs", [SPECS_2D, SPECS_3D], ids=["2d", "3d"])
+def test_every_launch_configuration_equals_alone(sw, specs, shape, schedule):
+    """Tile shapes and label schedules change no result: every member is
+    bit-identical to the same lattice advanced alone (shape-0 tiles)."""
+    dim = specs[0][1]
+    b = sw.sw_batch_create(dim)
+    inb = [make(sw, s, 700 + k) for k, s in enumerate(specs)]
+    alone = [make(sw, s, 700 + k) for k, s in enumerate(specs)]
+    try:
+        for h in inb:
+            sw.sw_batch_add(b, h)
+        sw.sw_batch_set_config(b, shape, schedule)
+        cfg = sw.sw_batch_get_config(b)
+        assert (cfg["shape"], cfg["schedule"]) == (shape, schedule)
+        assert cfg["tile_y"] == ([256, 128, 64] if dim == 2 else [16, 16, 8])[shape]
+        assert cfg["tile_z"] == (1 if dim == 2 else [16, 8, 8][shape])
+        sw.sw_batch_sweep(b, 5)
+        for h in alone:
+            sw.sw_sweep(h, 5)
+        for x, y in zip(inb, alone):
+            same_state(sw, x, y, 1, 5)
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in inb + alone:
+            sw.sw_destroy(h)
+
+
+def test_autotune_keeps_the_fastest_and_changes_no_result(sw):
+    specs = SPECS_2D
+    b = sw.sw_batch_create(2)
+    inb = [make(sw, s, 800 + k) for k, s in enumerate(specs)]
+    alone = [make(sw, s, 800 + k) for k, s in enumerate(specs)]
+    try:
+        for h in inb:
+            sw.sw_batch_add(b, h)
+        sw.sw_batch_sweep(b, 2)
+        ms = sw.sw_batch_autotune(b, 2)
+        # Ising and Potts members: every shape with both label schedules
+        assert ms.shape == (sw.SW_BATCH_TILE_SHAPES, sw.SW_BATCH_LABEL_SCHEDULES)
+        assert np.all(ms > 0)
+        cfg = sw.sw_batch_get_config(b)
+        assert ms[cfg["shape"], cfg["schedule"]] == ms.min()
+        tuned = 2 + ms.size * (2 + 1)       # each configuration: one untimed + two timed sweeps
+        for h in inb:
+            assert sw.sw_sweep_counter(h) == tuned
+        sw.sw_batch_sweep(b, 3)
+        # a configuration switch between calls, then more sweeps
+        sw.sw_batch_set_config(b, (cfg["shape"] + 1) % 3, 1 - cfg["schedule"])
+        sw.sw_batch_sweep(b, 2)
+        for h in alone:
+            sw.sw_sweep(h, tuned + 5)
+        for x, y in zip(inb, alone):
+            same_state(sw, x, y, tuned + 1, 4)
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in inb + alone:
+            sw.sw_destroy(h)
+
+
+def test_autotune_of_one_model_tries_one_schedule(sw):
+    b = sw.sw_batch_create(3)
+    hs = [make(sw, (ISING, 3, L, 2, 4.5115), 900 + L) for L in (16, 24)]
+    try:
+        for h in hs:
+            sw.sw_batch_add(b, h)
+        ms = sw.sw_batch_autotune(b, 1)
+        assert np.all(ms[:, 0] > 0) and np.all(ms[:, 1] == -1)
+        assert sw.sw_batch_get_config(b)["schedule"] == 0
+        for h in hs:
+            assert sw.sw_sweep_counter(h) == 3 * 2
+        with pytest.raises(sw.SwError):
+            sw.sw_batch_set_config(b, 3, 0)
+        with pytest.raises(sw.SwError):
+            sw.sw_batch_set_config(b, 0, 2)
+        with pytest.raises(sw.SwError):
+            sw.sw_batch_autotune(b, 0)
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in hs:
+            sw.sw_destroy(h)
