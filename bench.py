@@ -435,6 +435,44 @@ def _job_list(specs):
     return [Job(**d) for d in specs]
 
 
+def small_batch(sw, inputs, st, sweeps=50):
+    """256 small 2D lattices (seed 1005, L 16..90): one batch, every member
+    whole in one CTA's shared memory, against the same lattices one after
+    another (each a one-CTA launch of all its sweeps)."""
+    import torch
+    specs = inputs.small_batch(256, 1005)
+    sites = sum(L ** d for (_, d, L, _, _, _) in specs)
+    hs = [sw.sw_create(m, d, L, q, T, seed) for (m, d, L, q, T, seed) in specs]
+    b = sw.sw_batch_create(2)
+    sw.sw_batch_set_stream(b, st.cuda_stream)
+    for h in hs:
+        sw.sw_set_stream(h, st.cuda_stream)
+        sw.sw_batch_add(b, h)
+    sw.sw_batch_sweep(b, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    sw.sw_batch_sweep(b, sweeps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    sw.sw_batch_destroy(b)
+    e0.record(st)
+    for h in hs:
+        sw.sw_sweep(h, sweeps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_serial = e0.elapsed_time(e1) / 1e3
+    for h in hs:
+        sw.sw_destroy(h)
+    return {"workload": "256 2D lattices, model uniform over Ising / Potts q=3 / Potts q=4, L uniform in "
+                        "[16,90], T in [0.8,1.2] Tc, seed 1005, 50 measured sweeps",
+            "sites": sites, "value": sites * sweeps / (t_batch * 1e9), "unit": UNIT,
+            "ms_per_step": 1e3 * t_batch / sweeps,
+            "serial": {"value": sites * sweeps / (t_serial * 1e9), "unit": UNIT},
+            "speedup_vs_serial": t_serial / t_batch}
+
+
 def run_batch(args):
     """Ragged batch of 256 2D Ising/Potts lattices (seed 1003), advanced
     together (one launch per phase, graph-replayed sweeps) vs the same
@@ -483,6 +521,7 @@ def run_batch(args):
         sw.sw_destroy(h)
     v_batch = sites * args.steps / (t_batch * 1e9)
     v_serial = sites * k_serial / (t_serial * 1e9)
+    small = small_batch(sw, inputs, st)
     line = {"metric": "ragged batch site-updates/ns (256 2D Ising/Potts lattices, L 32..1024)",
             "value": v_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_batch / args.steps,
@@ -500,6 +539,7 @@ def run_batch(args):
                                                          for sh in range(tune_ms.shape[0])
                                                          for sc in range(tune_ms.shape[1]) if tune_ms[sh, sc] > 0},
                          "note": "5 timed sweeps per configuration, before the timed region"},
+            "small_lattices": small,
             # per step: labels of the Ising tiles and of the Potts tiles,
             # merge, compression, apply, step counter
             "gpu_launches": 6 * args.steps, "clocks": clk}

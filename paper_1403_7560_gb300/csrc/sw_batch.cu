@@ -39,6 +39,14 @@ struct sw_batch {
   uint32_t ising_tiles = 0;           // the tile map lists the Ising members' tiles first
   int shape = 0;                      // tile shape (index into the shape table)
   int schedule = 0;                   // label schedule (separate or one launch)
+  // small members (whole sweeps in one CTA's shared memory): member indices,
+  // the Ising ones then the Potts ones, run on a forked branch of the graph
+  uint32_t* d_small = nullptr;
+  size_t cap_small = 0;
+  uint32_t n_small_ising = 0, n_small_potts = 0;
+  std::vector<bool> is_small;         // per member
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev = nullptr;
 };
@@ -86,7 +94,17 @@ size_t member_tiles(const sw_batch* b, const sw_handle* h) {
 // or configuration.
 int rebuild(sw_batch* b) {
   size_t ntiles = 0;
-  for (sw_handle* h : b->members) ntiles += member_tiles(b, h);
+  std::vector<uint32_t> small_ising, small_potts;
+  b->is_small.assign(b->members.size(), false);
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    sw_handle* h = b->members[m];
+    if (swgb::small_lattice(h->lat)) {
+      b->is_small[m] = true;
+      (h->model == SW_POTTS ? small_potts : small_ising).push_back((uint32_t)m);
+    } else {
+      ntiles += member_tiles(b, h);
+    }
+  }
   if (ntiles > 0x7fffffffu) return bfail(SW_ERR_BAD_ARG, "batch has too many tiles");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch sync");
@@ -109,12 +127,36 @@ int rebuild(sw_batch* b) {
       return bfail(SW_ERR_OOM, std::string("batch tile map: ") + cudaGetErrorString(e));
     b->cap_tiles = cap;
   }
+  const size_t nsmall = small_ising.size() + small_potts.size();
+  if (nsmall > b->cap_small) {
+    cudaFree(b->d_small);
+    b->d_small = nullptr;
+    const size_t cap = std::max<size_t>(64, nsmall * 2);
+    if ((e = cudaMalloc(&b->d_small, cap * sizeof(uint32_t))) != cudaSuccess)
+      return bfail(SW_ERR_OOM, std::string("batch small-member list: ") + cudaGetErrorString(e));
+    b->cap_small = cap;
+  }
+  if (nsmall) {
+    std::vector<uint32_t> all(small_ising);
+    all.insert(all.end(), small_potts.begin(), small_potts.end());
+    if ((e = cudaMemcpy(b->d_small, all.data(), nsmall * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bcuda(e, "batch small-member list");
+    if (!b->side) {
+      if ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+        return bcuda(e, "batch side stream");
+    }
+    if ((e = swgb::prepare_small_batch()) != cudaSuccess) return bcuda(e, "small-lattice kernels");
+  }
+  b->n_small_ising = (uint32_t)small_ising.size();
+  b->n_small_potts = (uint32_t)small_potts.size();
   std::vector<uint32_t> lat(ntiles), idx(ntiles);
   size_t t = 0;
   for (int pass = 0; pass < 2; ++pass) {  // Ising members' tiles, then Potts
     for (size_t m = 0; m < b->members.size(); ++m) {
       const sw_handle* h = b->members[m];
-      if ((h->model == SW_POTTS) != (pass == 1)) continue;
+      if (b->is_small[m] || (h->model == SW_POTTS) != (pass == 1)) continue;
       const uint32_t n = (uint32_t)member_tiles(b, h);
       for (uint32_t k = 0; k < n; ++k, ++t) {
         lat[t] = (uint32_t)m;
@@ -130,16 +172,30 @@ int rebuild(sw_batch* b) {
   }
   b->ntiles = (uint32_t)ntiles;
   drop_graph(b);
-  if (ntiles) {
-    // capture one sweep: labels (+ measurement), merge, compression, apply, step
+  if (ntiles || nsmall) {
+    // capture one sweep: the small members on a forked branch; labels (+
+    // measurement), merge, compression, apply of the tiled ones; the step
     cudaGraph_t g = nullptr;
     const BatchView v = view(b);
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t le = swgb::launch_label_batch(v, b->dim, b->shape, b->schedule, b->ising_tiles,
-                                                b->ntiles - b->ising_tiles, b->stream);
-      if (le == cudaSuccess) le = swgb::launch_merge_batch(v, b->dim, b->shape, b->ntiles, b->stream);
-      if (le == cudaSuccess) le = swgb::launch_flip_batch(v, b->dim, b->shape, b->ntiles, b->stream);
+      cudaError_t le = cudaSuccess;
+      if (nsmall) {
+        le = cudaEventRecord(b->ev_fork, b->stream);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+        if (le == cudaSuccess)
+          le = swgb::launch_small_batch(v, b->dim, b->d_small, b->n_small_ising, b->d_small + b->n_small_ising,
+                                        b->n_small_potts, b->side);
+        if (le == cudaSuccess) le = cudaEventRecord(b->ev_join, b->side);
+      }
+      if (le == cudaSuccess && ntiles) {
+        le = swgb::launch_label_batch(v, b->dim, b->shape, b->schedule, b->ising_tiles, b->ntiles - b->ising_tiles,
+                                      b->stream);
+        if (le == cudaSuccess) le = swgb::launch_merge_batch(v, b->dim, b->shape, b->ntiles, b->stream);
+        if (le == cudaSuccess) le = swgb::launch_flip_batch(v, b->dim, b->shape, b->ntiles, b->stream);
+      }
+      if (le == cudaSuccess && nsmall) le = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+      if (le == cudaSuccess) le = swgb::launch_advance(v, b->stream);
       e = cudaStreamEndCapture(b->stream, &g);
       if (e == cudaSuccess) e = le;
     }
@@ -190,7 +246,11 @@ void sw_batch_destroy(sw_batch* b) {
   cudaFree(b->d_members);
   cudaFreeHost(b->h_members);
   cudaFree(b->d_tiles);
+  cudaFree(b->d_small);
   cudaFree(b->d_step);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -285,10 +345,13 @@ int batch_sweep(sw_batch* b, int n, float* ms) {
   // later work on each member waits for the batch
   if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->stream);
   if (e == cudaSuccess) {
-    for (sw_handle* h : b->members) {
+    for (size_t m = 0; m < b->members.size(); ++m) {
+      sw_handle* h = b->members[m];
       if ((e = cudaStreamWaitEvent(h->stream, b->ev, 0)) != cudaSuccess) break;
       h->sweep += (uint64_t)n;
-      h->pending = h->sweep;  // the last sweep's record, written on demand
+      // a tiled member's last record is written on demand; a small member
+      // writes every record in its sweep
+      h->pending = b->is_small[m] ? 0 : h->sweep;
     }
   }
   if (e == cudaSuccess && ms) e = cudaEventSynchronize(t1);

@@ -383,7 +383,6 @@ template <int D, int SH>
 cudaError_t flip_batch_shape(const BatchView& bv, uint32_t ntiles, cudaStream_t st) {
   cudaError_t e = launch_pdl(k_compress_batch, ntiles, kFlipThreads, st, bv);
   if (e == cudaSuccess) e = launch_pdl(k_apply_batch<ShapeOf<D, SH>>, ntiles, kFlipThreads, st, bv);
-  if (e == cudaSuccess) e = launch_pdl(k_advance, 1u, 1u, st, bv.step);
   return e;
 }
 
@@ -410,6 +409,11 @@ cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, uint32_t
 
 cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st) {
   return dim == 2 ? flip_batch_dim<2>(bv, shape, ntiles, st) : flip_batch_dim<3>(bv, shape, ntiles, st);
+}
+
+cudaError_t launch_advance(const BatchView& bv, cudaStream_t st) {
+  k_advance<<<1, 1, 0, st>>>(bv.step);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st) {

@@ -179,6 +179,15 @@ cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int sche
                                uint32_t potts_tiles, cudaStream_t st);
 cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st);
 cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st);
+// Advances the batch step counter (after every member's sweep).
+cudaError_t launch_advance(const BatchView& bv, cudaStream_t st);
+// Small members of a batch (sw_small.cu): one CTA per member, whole sweeps
+// in shared memory; lists of member indices, Ising and Potts.
+// prepare_small_batch sets the kernels' shared-memory limit (once, before
+// capture).
+cudaError_t prepare_small_batch();
+cudaError_t launch_small_batch(const BatchView& bv, int dim, const uint32_t* ising_list, uint32_t n_ising,
+                               const uint32_t* potts_list, uint32_t n_potts, cudaStream_t st);
 
 // Write the record of a pending measured sweep of h (stand-alone kernel).
 cudaError_t flush_pending(struct ::sw_handle* h);

@@ -32,7 +32,7 @@ struct SmallLayout {
   size_t par, planes, draws, starts, spins, pdraw, total;
 };
 
-SmallLayout small_layout(const Lattice& lat, bool potts) {
+__host__ __device__ SmallLayout small_layout(const Lattice& lat, bool potts) {
   const size_t rw = (size_t)lat.R * (size_t)lat.W;
   SmallLayout s;
   s.par = 0;
@@ -46,14 +46,21 @@ SmallLayout small_layout(const Lattice& lat, bool potts) {
   return s;
 }
 
+// Shared memory of a small sweep besides the dynamic lattice block.
+struct SmallScratch {
+  long long s_ri[kSmallWarps];
+  unsigned int s_hist[256];
+  double s_acc[6];  // the FP64 accumulators, written back at the end
+};
+
+// n sweeps after sweep0 of one small lattice by the whole CTA.
 template <int D, bool POTTS>
-__global__ void __launch_bounds__(kSmallThreads, 1)
-    k_sweep_small(const __grid_constant__ Lattice lat, const __grid_constant__ Measure mb, uint32_t sweep0,
-                  int n, int measure, SmallLayout lay) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long s_ri[kSmallWarps];
-  __shared__ unsigned int s_hist[256];
-  __shared__ double s_acc[6];  // the FP64 accumulators, written back at the end
+__device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& mb, uint32_t sweep0, int n,
+                                            bool measure, const SmallLayout& lay, unsigned char* smem,
+                                            SmallScratch& sc) {
+  long long* s_ri = sc.s_ri;
+  unsigned int* s_hist = sc.s_hist;
+  double* s_acc = sc.s_acc;
   uint32_t* par = reinterpret_cast<uint32_t*>(smem + lay.par);
   uint32_t* pl = reinterpret_cast<uint32_t*>(smem + lay.planes);
   uint32_t* dw = reinterpret_cast<uint32_t*>(smem + lay.draws);
@@ -211,6 +218,31 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
 }
 
 template <int D, bool POTTS>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    k_sweep_small(const __grid_constant__ Lattice lat, const __grid_constant__ Measure mb, uint32_t sweep0,
+                  int n, int measure, SmallLayout lay) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SmallScratch sc;
+  sweep_small<D, POTTS>(lat, mb, sweep0, n, measure != 0, lay, smem, sc);
+}
+
+// Small members of a batch, one CTA per member (list[blockIdx.x]), one
+// measured sweep per launch: sweep number from the batch step counter.
+template <int D, bool POTTS>
+__global__ void __launch_bounds__(kSmallThreads, 1) k_sweep_small_batch(BatchView bv, const uint32_t* list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SmallScratch sc;
+  __shared__ Lattice s_lat;  // read on every Philox round
+  static_assert(sizeof(Lattice) % 4 == 0 && sizeof(Lattice) / 4 <= kSmallThreads, "lattice copy");
+  const BatchMember& m = bv.members[__ldg(&list[blockIdx.x])];
+  if (threadIdx.x < sizeof(Lattice) / 4)
+    reinterpret_cast<uint32_t*>(&s_lat)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&m.lat)[threadIdx.x];
+  __syncthreads();
+  const SmallLayout lay = small_layout(s_lat, POTTS);
+  sweep_small<D, POTTS>(s_lat, m.meas, m.sweep0 + *bv.step, 1, true, lay, smem, sc);
+}
+
+template <int D, bool POTTS>
 cudaError_t launch_small_t(const Lattice& lat, const Measure& m, uint32_t sweep0, int n, bool measure,
                            cudaStream_t st) {
   const SmallLayout lay = small_layout(lat, POTTS);
@@ -243,6 +275,32 @@ bool small_lattice(const Lattice& lat) {
   // (L <= 90) and 4096 in 3D (L <= 16)
   if (lat.N > (uint32_t)(lat.dim == 2 ? kSmallSites : kSmallSites / 2)) return false;
   return small_layout(lat, lat.model == kPotts).total <= small_layout_bytes_max();
+}
+
+cudaError_t prepare_small_batch() {
+  const int bytes = (int)small_layout_bytes_max();
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_small_batch<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_small_batch<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_small_batch<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_small_batch<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+cudaError_t launch_small_batch(const BatchView& bv, int dim, const uint32_t* ising_list, uint32_t n_ising,
+                               const uint32_t* potts_list, uint32_t n_potts, cudaStream_t st) {
+  const size_t bytes = small_layout_bytes_max();
+  if (n_ising) {
+    if (dim == 2) k_sweep_small_batch<2, false><<<n_ising, kSmallThreads, bytes, st>>>(bv, ising_list);
+    else k_sweep_small_batch<3, false><<<n_ising, kSmallThreads, bytes, st>>>(bv, ising_list);
+  }
+  if (n_potts) {
+    if (dim == 2) k_sweep_small_batch<2, true><<<n_potts, kSmallThreads, bytes, st>>>(bv, potts_list);
+    else k_sweep_small_batch<3, true><<<n_potts, kSmallThreads, bytes, st>>>(bv, potts_list);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sweeps_small(const Lattice& lat, const Measure& m, uint32_t sweep0, int n, bool measure,

@@ -130,6 +130,23 @@ def ragged_batch(n: int = 256, seed: int = 1003):
     return out
 
 
+def small_batch(n: int = 256, seed: int = 1005):
+    """Many small lattices: n 2D lattices, model uniform over {Ising, Potts
+    q=3, Potts q=4}, L uniform over [16, 90] (at most 8192 sites, the
+    one-CTA path), T uniform in [0.8 Tc, 1.2 Tc], one seed per lattice.
+    Returns a list of (model, dim, L, q, T, seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        kind = int(rng.integers(0, 3))
+        model, q = (ISING, 2) if kind == 0 else (POTTS, 3 if kind == 1 else 4)
+        L = int(rng.integers(16, 91))
+        tc = TC_2D_ISING if model == ISING else tc_2d_potts(q)
+        T = tc * float(rng.uniform(0.8, 1.2))
+        out.append((model, 2, L, q, T, int(rng.integers(1, 2 ** 62))))
+    return out
+
+
 def served_stream(n: int, seed: int = 1004, rate: float | None = None, max_L2: int = 4096,
                   max_L3: int = 256, sweeps=(100, 5000)):
     """The served request stream: n jobs, class uniform over {2D Ising, 3D

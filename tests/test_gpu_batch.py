@@ -222,3 +222,42 @@ def test_autotune_of_one_model_tries_one_schedule(sw):
         sw.sw_batch_destroy(b)
         for h in hs:
             sw.sw_destroy(h)
+
+
+def test_small_members_run_whole_in_shared_memory(sw):
+    """Members of at most 8192 sites (2D) or 4096 (3D) take the one-CTA
+    branch of the batch graph; a batch of many of them, Ising and Potts,
+    with a large member beside them, stays bit-identical to every lattice
+    advanced alone, across a member leaving."""
+    rng = np.random.default_rng(11)
+    specs = []
+    for k in range(40):
+        L = int(rng.integers(8, 91))
+        if k % 3 == 0:
+            specs.append((ISING, 2, L, 2, 2.269185 * float(rng.uniform(0.9, 1.1))))
+        else:
+            q = int(rng.choice([3, 4, 8]))
+            specs.append((POTTS, 2, L, q, 1.0 / np.log(1 + np.sqrt(q)) * float(rng.uniform(0.9, 1.1))))
+    specs.append((ISING, 2, 200, 2, 2.269185))
+    b = sw.sw_batch_create(2)
+    inb = [make(sw, s, 1200 + k) for k, s in enumerate(specs)]
+    alone = [make(sw, s, 1200 + k) for k, s in enumerate(specs)]
+    try:
+        for h in inb:
+            sw.sw_batch_add(b, h)
+        sw.sw_batch_sweep(b, 7)
+        for h in alone:
+            sw.sw_sweep(h, 7)
+        for x, y in zip(inb, alone):
+            same_state(sw, x, y, 1, 7)
+        sw.sw_batch_remove(b, inb[0])
+        sw.sw_batch_sweep(b, 3)
+        sw.sw_sweep(inb[0], 3)
+        for h in alone:
+            sw.sw_sweep(h, 3)
+        for x, y in zip(inb, alone):
+            same_state(sw, x, y, 8, 3)
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in inb + alone:
+            sw.sw_destroy(h)
