@@ -435,6 +435,17 @@ def _job_list(specs):
     return [Job(**d) for d in specs]
 
 
+def batch_launches(specs, schedule):
+    """Kernels one batch sweep launches: the tiled members' labels (one
+    launch per model under schedule 0, one in all under schedule 1), merge,
+    compression and apply; one launch per model of the small members (at
+    most 8192 sites in 2D); the step counter."""
+    tiled = {m for (m, d, L, _, _, _) in specs if L ** d > 8192}
+    small = {m for (m, d, L, _, _, _) in specs if L ** d <= 8192}
+    labels = (len(tiled) if schedule == 0 else 1) if tiled else 0
+    return labels + (3 if tiled else 0) + len(small) + 1
+
+
 def small_batch(sw, inputs, st, sweeps=50):
     """256 small 2D lattices (seed 1005, L 16..90): one batch, every member
     whole in one CTA's shared memory, against the same lattices one after
@@ -470,7 +481,8 @@ def small_batch(sw, inputs, st, sweeps=50):
             "sites": sites, "value": sites * sweeps / (t_batch * 1e9), "unit": UNIT,
             "ms_per_step": 1e3 * t_batch / sweeps,
             "serial": {"value": sites * sweeps / (t_serial * 1e9), "unit": UNIT},
-            "speedup_vs_serial": t_serial / t_batch}
+            "speedup_vs_serial": t_serial / t_batch,
+            "gpu_launches": batch_launches(specs, 0) * sweeps}
 
 
 def run_batch(args):
@@ -540,9 +552,7 @@ def run_batch(args):
                                                          for sc in range(tune_ms.shape[1]) if tune_ms[sh, sc] > 0},
                          "note": "5 timed sweeps per configuration, before the timed region"},
             "small_lattices": small,
-            # per step: labels of the Ising tiles and of the Potts tiles,
-            # merge, compression, apply, step counter
-            "gpu_launches": 6 * args.steps, "clocks": clk}
+            "gpu_launches": batch_launches(specs, cfg["schedule"]) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
