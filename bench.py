@@ -439,9 +439,11 @@ def batch_launches(specs, schedule):
     """Kernels one batch sweep launches: the tiled members' labels (one
     launch per model under schedule 0, one in all under schedule 1), merge,
     compression and apply; one launch per model of the small members (at
-    most 8192 sites in 2D); the step counter."""
-    tiled = {m for (m, d, L, _, _, _) in specs if L ** d > 8192}
-    small = {m for (m, d, L, _, _, _) in specs if L ** d <= 8192}
+    most 8192 sites in 2D, 4096 in 3D); the step counter."""
+    def is_small(d, L):
+        return L ** d <= (8192 if d == 2 else 4096)
+    tiled = {m for (m, d, L, _, _, _) in specs if not is_small(d, L)}
+    small = {m for (m, d, L, _, _, _) in specs if is_small(d, L)}
     labels = (len(tiled) if schedule == 0 else 1) if tiled else 0
     return labels + (3 if tiled else 0) + len(small) + 1
 
