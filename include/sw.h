@@ -254,6 +254,13 @@ size_t sw_series_capacity(void);
  *                          afterwards each member's counter has advanced by n
  *                          and its records and accumulators are read with the
  *                          usual per-handle calls, which wait for the batch.
+ *                          A member with a sweep target (below) advances by
+ *                          min(n, target - counter) only, 0 once there.
+ * sw_set_sweep_target(h, t)  batch sweeps of h stop when its counter
+ *                          reaches t (t = 0: no target; t >= 2^32 - 1 is
+ *                          SW_ERR_BAD_ARG).  Single-lattice calls ignore it.
+ *                          A serving loop gives each job its sweep count and
+ *                          advances the whole batch by a fixed chunk.
  * sw_batch_set_stream      run on a caller's non-default stream instead.
  * sw_batch_size            number of members.
  * sw_batch_destroy(b)      frees the batch (not its members).  sw_destroy of a
@@ -287,7 +294,9 @@ size_t sw_series_capacity(void);
  *                          floats, index shape * 2 + schedule) receives the
  *                          time per sweep of each configuration, -1 where not
  *                          tried.  An empty batch returns SW_OK untouched;
- *                          sweeps < 1 is SW_ERR_BAD_ARG. */
+ *                          sweeps < 1, or a member whose sweep target lies
+ *                          within the C * (sweeps + 1) sweeps, is
+ *                          SW_ERR_BAD_ARG. */
 #define SW_BATCH_TILE_SHAPES 3
 #define SW_BATCH_LABEL_SCHEDULES 2
 typedef struct sw_batch sw_batch;
@@ -299,6 +308,7 @@ int sw_batch_sweep(sw_batch* b, int n);
 int sw_batch_set_stream(sw_batch* b, void* stream);
 size_t sw_batch_size(sw_batch* b);
 size_t sw_device_bytes(int model, int dim, int L, int q);
+int sw_set_sweep_target(sw_handle* h, uint64_t target);
 int sw_batch_set_config(sw_batch* b, int shape, int schedule);
 int sw_batch_get_config(const sw_batch* b, int* shape, int* schedule, int* tile_y, int* tile_z);
 int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep);

@@ -302,32 +302,45 @@ int sw_batch_set_stream(sw_batch* b, void* stream) {
 
 namespace {
 
-// n sweeps of every member (graph replays); with ms != nullptr the replays
-// alone are timed with events on the batch stream (a host wait).
+// Up to n sweeps of every member (graph replays): a member with a sweep
+// target stops there.  With ms != nullptr the replays alone are timed with
+// events on the batch stream (a host wait).
 int batch_sweep(sw_batch* b, int n, float* ms) {
   if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
   if (n < 0) return bfail(SW_ERR_BAD_ARG, "n < 0");
   if (n == 0 || b->members.empty()) return SW_OK;
-  for (sw_handle* h : b->members)
-    if (h->sweep + (uint64_t)n >= 0xffffffffull) return bfail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+  std::vector<uint32_t> count(b->members.size());
+  uint32_t replays = 0;
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    const sw_handle* h = b->members[m];
+    uint64_t c = (uint64_t)n;
+    if (h->target) c = h->target > h->sweep ? std::min<uint64_t>(c, h->target - h->sweep) : 0;
+    if (h->sweep + c >= 0xffffffffull) return bfail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+    count[m] = (uint32_t)c;
+    replays = std::max(replays, count[m]);
+  }
+  if (replays == 0) return SW_OK;
   if (b->dirty) {
     const int rc = rebuild(b);
     if (rc != SW_OK) return rc;
   }
-  // every member's earlier work (and its pending record) precedes the batch
+  // every member's earlier work precedes the batch; a tiled member's pending
+  // record (of its current state) is measured by the batch's first step
   cudaError_t e = cudaStreamSynchronize(b->stream);  // the staging copy below is reused
-  for (sw_handle* h : b->members) {
-    if (e == cudaSuccess) e = swgb::flush_pending(h);
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    sw_handle* h = b->members[m];
+    const bool measure0 = !b->is_small[m] && count[m] > 0 && h->pending != 0 && h->pending == h->sweep;
+    if (e == cudaSuccess && count[m] > 0 && !measure0) e = swgb::flush_pending(h);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev, h->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev, 0);
-  }
-  if (e != cudaSuccess) return bcuda(e, "batch ordering");
-  for (size_t m = 0; m < b->members.size(); ++m) {
-    const sw_handle* h = b->members[m];
     b->h_members[m].lat = member_view(b, h);
     b->h_members[m].meas = h->meas;
     b->h_members[m].sweep0 = (uint32_t)h->sweep;
+    b->h_members[m].nsweeps = count[m];
+    b->h_members[m].measure0 = measure0 ? 1u : 0u;
+    if (measure0) h->pending = 0;  // written by the batch
   }
+  if (e != cudaSuccess) return bcuda(e, "batch ordering");
   if ((e = cudaMemcpyAsync(b->d_members, b->h_members, b->members.size() * sizeof(BatchMember),
                            cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(b->d_step, 0, sizeof(uint32_t), b->stream)) != cudaSuccess)
@@ -340,7 +353,7 @@ int batch_sweep(sw_batch* b, int n, float* ms) {
       return bcuda(e, "batch timing");
     }
   }
-  for (int s = 0; s < n && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->graph, b->stream);
+  for (uint32_t s = 0; s < replays && e == cudaSuccess; ++s) e = cudaGraphLaunch(b->graph, b->stream);
   if (e == cudaSuccess && ms) e = cudaEventRecord(t1, b->stream);
   // later work on each member waits for the batch
   if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->stream);
@@ -348,10 +361,11 @@ int batch_sweep(sw_batch* b, int n, float* ms) {
     for (size_t m = 0; m < b->members.size(); ++m) {
       sw_handle* h = b->members[m];
       if ((e = cudaStreamWaitEvent(h->stream, b->ev, 0)) != cudaSuccess) break;
-      h->sweep += (uint64_t)n;
+      if (count[m] == 0) continue;
+      h->sweep += count[m];
       // a tiled member's last record is written on demand; a small member
       // writes every record in its sweep
-      h->pending = b->is_small[m] ? 0 : h->sweep;
+      if (!b->is_small[m]) h->pending = h->sweep;
     }
   }
   if (e == cudaSuccess && ms) e = cudaEventSynchronize(t1);
@@ -402,8 +416,12 @@ int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep) {
   // one label launch differs from two only when both kinds are present
   const int schedules = (ising && potts) ? swgb::kLabelSchedules : 1;
   const uint64_t total = (uint64_t)swgb::kTileShapes * schedules * ((uint64_t)sweeps + 1);
-  for (const sw_handle* h : b->members)
+  for (const sw_handle* h : b->members) {
     if (h->sweep + total >= 0xffffffffull) return bfail(SW_ERR_BAD_ARG, "sweep counter exhausted");
+    // every configuration must time the same members
+    if (h->target && h->target < h->sweep + total)
+      return bfail(SW_ERR_BAD_ARG, "a member's sweep target falls within the tuning sweeps");
+  }
   int best_shape = b->shape, best_schedule = b->schedule;
   float best = -1.0f;
   for (int sh = 0; sh < swgb::kTileShapes; ++sh) {

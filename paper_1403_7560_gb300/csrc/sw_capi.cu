@@ -438,6 +438,13 @@ int sw_set_sweep_counter(sw_handle* h, uint64_t k) {
   return SW_OK;
 }
 
+int sw_set_sweep_target(sw_handle* h, uint64_t target) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  if (target >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep target must be < 2^32 - 1");
+  h->target = target;
+  return SW_OK;
+}
+
 size_t sw_num_sites(sw_handle* h) { return h ? h->lat.N : 0; }
 size_t sw_spin_bytes(sw_handle* h) { return h ? h->spin_bytes : 0; }
 size_t sw_bond_words(sw_handle* h) { return h ? h->bond_words : 0; }

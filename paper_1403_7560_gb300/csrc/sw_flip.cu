@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_
   __shared__ MergeSmem<S> sm;
   pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
+  if (*bv.step >= m.nsweeps) return;  // the member has had its sweeps this call
   merge_tile<S>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
 }
 
@@ -184,7 +185,9 @@ __global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const uint32_t step = *bv.step;
-  if (tile == 0u && step > 0u) finalize_record<kFlipWarps>(m.lat, m.meas, m.sweep0 + step, s_red, s_rd);
+  if (step >= m.nsweeps) return;
+  if (tile == 0u && (step > 0u || m.measure0))
+    finalize_record<kFlipWarps>(m.lat, m.meas, m.sweep0 + step, s_red, s_rd);
   compress_tile(m.lat, tile);
 }
 
@@ -267,7 +270,9 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   const Lattice& lat = m.lat;
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
-  const uint32_t sweep = m.sweep0 + *bv.step + 1u;
+  const uint32_t step = *bv.step;
+  if (step >= m.nsweeps) return;
+  const uint32_t sweep = m.sweep0 + step + 1u;
   const TileCoord tc = tile_coord<S>(lat, tile);
   const int L = lat.L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sb = lat.sbits, shift = sb + 1;

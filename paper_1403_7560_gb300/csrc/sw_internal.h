@@ -72,6 +72,8 @@ struct BatchMember {
   Lattice lat;
   Measure meas;
   uint32_t sweep0;
+  uint32_t nsweeps;   // sweeps of this member in the current batch call (steps >= nsweeps skip it)
+  uint32_t measure0;  // 1: the first step also measures the incoming state (the record of sweep0)
 };
 
 // Device-side description of a batch: members, the tile -> (member, tile)
@@ -223,6 +225,7 @@ struct sw_handle {
   swgb::Lattice lat{};
   swgb::Measure meas{};
   uint64_t pending = 0;         // measured sweep whose record is not yet written
+  uint64_t target = 0;          // batch sweeps stop at this counter value (0: no target)
   int32_t* d_labels = nullptr;  // debug readout buffer, allocated on first use
   void* d_block = nullptr;      // one allocation holding every small buffer
   void* d_clock = nullptr;      // clock model: thresholds, fixed-point cos/sin, slot sums

@@ -314,8 +314,10 @@ __global__ void __launch_bounds__(kTileThreads, 5) k_label(const __grid_constant
 
 // Ising/Potts lattices of a batch, one tile of shape S per CTA; sweep
 // numbers come from the batch step counter, and every step after the first
-// also measures the incoming state of its lattice (the record of the
-// previous sweep).  The tile map lists the Ising members' tiles first.
+// (the first too when the member's last record is pending) also measures
+// the incoming state of its lattice (the record of the previous sweep).  A
+// member stops after its own number of sweeps.  The tile map lists the
+// Ising members' tiles first.
 // LAYOUT 1: Ising tiles only, two-state layout; LAYOUT 2: Potts tiles only;
 // LAYOUT 3: any tile, Potts layout, the member's model picked per tile.
 // Resident CTAs per SM: five 256-thread CTAs (two-state layout) or four
@@ -340,9 +342,10 @@ __global__ void __launch_bounds__(S::THREADS, label_blocks(S::THREADS, LAYOUT))
     reinterpret_cast<uint32_t*>(&s_lat)[k] = reinterpret_cast<const uint32_t*>(&m.lat)[k];
   __syncthreads();
   const uint32_t step = *bv.step;
+  if (step >= m.nsweeps) return;  // the member has had its sweeps this call
   const uint32_t sweep = m.sweep0 + step + 1u;
   const bool potts = LAYOUT == 2 || (LAYOUT == 3 && s_lat.model == kPotts);
-  if (step == 0u) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
+  if (step == 0u && !m.measure0) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
   else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
   else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
 }

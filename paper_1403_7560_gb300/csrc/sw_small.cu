@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
 }
 
 // Small members of a batch, one CTA per member (list[blockIdx.x]), one
-// measured sweep per launch: sweep number from the batch step counter.
+// measured sweep per launch: sweep number from the batch step counter; a
+// member stops after its own number of sweeps.
 template <int D, bool POTTS>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_sweep_small_batch(BatchView bv, const uint32_t* list) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_sweep_small_batch(BatchVie
   __shared__ Lattice s_lat;  // read on every Philox round
   static_assert(sizeof(Lattice) % 4 == 0 && sizeof(Lattice) / 4 <= kSmallThreads, "lattice copy");
   const BatchMember& m = bv.members[__ldg(&list[blockIdx.x])];
+  if (*bv.step >= m.nsweeps) return;  // the member has had its sweeps this call
   if (threadIdx.x < sizeof(Lattice) / 4)
     reinterpret_cast<uint32_t*>(&s_lat)[threadIdx.x] = reinterpret_cast<const uint32_t*>(&m.lat)[threadIdx.x];
   __syncthreads();

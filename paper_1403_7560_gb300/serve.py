@@ -7,9 +7,10 @@ engine admits queued jobs, oldest first, while their device footprint
 ragged batch of their dimension, so one launch per phase advances all of
 them.  XY jobs run on their own handle and stream and overlap with the
 batches.  Every engine iteration advances each active job by
-min(chunk, its remaining sweeps) -- one batch call per dimension with the
-smallest remaining count of its members -- then retires finished jobs,
-which frees budget for the queue.  Results do not depend on the mix: the
+min(chunk, its remaining sweeps) -- one batch call of chunk sweeps per
+dimension, each member stopping at its own sweep target (the job's sweep
+count, sw_set_sweep_target) -- then retires finished jobs, which frees
+budget for the queue.  Results do not depend on the mix: the
 random numbers are keyed by seed, sweep, site and purpose only.
 
 `run_serial` is the one-job-at-a-time plain path used as the comparison:
@@ -97,6 +98,7 @@ class Server:
             self.queue.pop(0)
             h = sw.sw_create(job.model, job.dim, job.L, job.q, job.T, job.seed)
             if job.model != sw.SW_XY:
+                sw.sw_set_sweep_target(h, job.sweeps)
                 sw.sw_batch_add(self.batches[job.dim], h)
             self.used += nbytes
             job.start = now
@@ -109,10 +111,10 @@ class Server:
             (xy if a.job.model == sw.SW_XY else groups[a.job.dim]).append(a)
         for dim, members in groups.items():
             if members:
-                n = min(self.chunk, min(a.remaining for a in members))
-                sw.sw_batch_sweep(self.batches[dim], n)
+                # every member stops at its own target
+                sw.sw_batch_sweep(self.batches[dim], self.chunk)
                 for a in members:
-                    a.done += n
+                    a.done += min(self.chunk, a.remaining)
         for a in xy:
             n = min(self.chunk, a.remaining)
             sw.sw_sweep(a.handle, n)

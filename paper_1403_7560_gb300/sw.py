@@ -79,6 +79,7 @@ _SIGNATURES = {
     "sw_batch_set_stream": (_i, [_vp, _vp]),
     "sw_batch_size": (_sz, [_vp]),
     "sw_device_bytes": (_sz, [_i, _i, _i, _i]),
+    "sw_set_sweep_target": (_i, [_vp, _u64]),
     "sw_batch_set_config": (_i, [_vp, _i, _i]),
     "sw_batch_get_config": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                                  ctypes.POINTER(_i)]),
@@ -347,6 +348,11 @@ def sw_batch_set_stream(b: Batch, stream: int):
 
 def sw_batch_size(b: Batch) -> int:
     return int(lib().sw_batch_size(b))
+
+
+def sw_set_sweep_target(h: Handle, target: int):
+    """Batch sweeps of h stop when its sweep counter reaches target (0: none)."""
+    _check(lib().sw_set_sweep_target(h, target))
 
 
 def sw_batch_set_config(b: Batch, shape: int, schedule: int):

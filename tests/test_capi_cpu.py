@@ -73,6 +73,7 @@ def test_null_handle_calls_fail_cleanly(swlib):
     assert lib.sw_batch_set_config(None, 0, 0) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_batch_get_config(None, None, None, None, None) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_batch_autotune(None, 1, None) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_set_sweep_target(None, 5) == swlib.SW_ERR_BAD_ARG
     lib.sw_destroy(None)
     assert swlib.sw_series_capacity() >= 1024
 

@@ -261,3 +261,43 @@ def test_small_members_run_whole_in_shared_memory(sw):
         sw.sw_batch_destroy(b)
         for h in inb + alone:
             sw.sw_destroy(h)
+
+
+def test_sweep_targets_and_first_step_measurement(sw):
+    """Members stop at their own sweep targets within one batch call; a
+    member arriving with a pending record (sweeps run alone) has it measured
+    by the batch's first step.  Every lattice stays bit-identical to the same
+    lattice advanced alone by the same number of sweeps."""
+    specs = SPECS_2D + [(ISING, 2, 160, 2, 2.3), (POTTS, 2, 130, 3, 1.0)]
+    targets = [5, 12, 0, 9, 3, 17, 11, 14, 8]
+    b = sw.sw_batch_create(2)
+    inb = [make(sw, s, 1500 + k) for k, s in enumerate(specs)]
+    alone = [make(sw, s, 1500 + k) for k, s in enumerate(specs)]
+    try:
+        sw.sw_sweep(inb[6], 2)             # tiled (L = 300): its sweep-2 record is pending
+        sw.sw_sweep(inb[7], 1)
+        for h, t in zip(inb, targets):
+            sw.sw_set_sweep_target(h, t)
+            sw.sw_batch_add(b, h)
+        sw.sw_batch_sweep(b, 4)
+        sw.sw_batch_sweep(b, 4)
+        sw.sw_batch_sweep(b, 10)
+        for k, (h, t) in enumerate(zip(inb, targets)):
+            expect = t if t else 18
+            assert sw.sw_sweep_counter(h) == expect, k
+            sw.sw_sweep(alone[k], expect)
+        for x, y, t in zip(inb, alone, targets):
+            n = sw.sw_sweep_counter(y)
+            same_state(sw, x, y, 1, n)
+        # a reached target stops the member; clearing it resumes
+        sw.sw_batch_sweep(b, 3)
+        assert sw.sw_sweep_counter(inb[0]) == 5
+        sw.sw_set_sweep_target(inb[0], 0)
+        sw.sw_batch_sweep(b, 2)
+        assert sw.sw_sweep_counter(inb[0]) == 7
+        with pytest.raises(sw.SwError):
+            sw.sw_batch_autotune(b, 1)     # targets inside the tuning sweeps
+    finally:
+        sw.sw_batch_destroy(b)
+        for h in inb + alone:
+            sw.sw_destroy(h)
