@@ -168,6 +168,9 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
 // (sums, then a one-block finalisation).
 cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const Measure& m,
                            cudaStream_t st);
+// The sums of the stand-alone Ising/Potts measurement (a thread per row
+// word, sw_label.cu); launch_measure adds the finalisation.
+cudaError_t launch_measure_rows(const Lattice& lat, const Measure& m, cudaStream_t st);
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);
 
 // Batched phases: one launch over every tile of every member (Ising/Potts,

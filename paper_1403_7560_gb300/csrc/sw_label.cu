@@ -82,6 +82,40 @@ __device__ __forceinline__ void load_rows(const uint8_t* s, int L, int x0, uint3
   }
 }
 
+// Measurement of one 32-site row word from its bytes and the equality masks
+// e0..e2 with its +x/+y/+z neighbours.  MM 1 (Ising): M = #(+1) - #(-1) and
+// E = -(#parallel - #antiparallel) over the +d bonds.  MM 2 (Potts): E = the
+// number of unequal +d bonds, and the histogram n[k] of the states (per-warp
+// bins for q <= kSmallQ, shared bins above).
+template <int D, int MM>
+__device__ __forceinline__ void measure_row(const RowBytes& rb, uint32_t e0, uint32_t e1, uint32_t e2,
+                                            uint32_t vmask, int nvalid, int q, int& m_acc, int& e_acc,
+                                            unsigned int* warp_hist, unsigned int* s_hist) {
+  const int par_bonds = __popc(e0) + __popc(e1) + (D == 3 ? __popc(e2) : 0);
+  if (MM == 1) {
+    uint32_t ones[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ones[k] = 0x01010101u;
+    m_acc += 2 * __popc(eq_bits(rb.a, ones) & vmask) - nvalid;
+    e_acc -= 2 * par_bonds - D * nvalid;
+  } else if (MM == 2) {
+    e_acc += D * nvalid - par_bonds;
+    if (q <= kSmallQ) {
+      for (int k = 0; k < q; ++k) {
+        uint32_t kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) kk[j] = 0x01010101u * (uint32_t)k;
+        const unsigned c = (unsigned)__popc(eq_bits(rb.a, kk) & vmask);
+        if (c) atomicAdd(&warp_hist[k], c);
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 32; ++b)
+        if (b < nvalid) atomicAdd(&s_hist[(rb.a[b >> 2] >> (8 * (b & 3))) & 0xffu], 1u);
+    }
+  }
+}
+
 // MM (measurement mode) 1 = Ising, 2 = Potts: also measure the incoming
 // spins (the state after sweep - 1): M and E from the row words' equality
 // masks and the Potts histogram, added to the measurement slots (the flip
@@ -179,32 +213,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
       const uint32_t e0 = eq_bits(rb.a, rb.ax) & vmask;
       const uint32_t e1 = eq_bits(rb.a, rb.ay) & vmask;
       const uint32_t e2 = (D == 3) ? (eq_bits(rb.a, rb.az) & vmask) : 0u;
-      if (MM == 1) {
-        // M = #(+1) - #(-1);  E = -(#parallel - #antiparallel) over the +d bonds
-        uint32_t ones[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) ones[k] = 0x01010101u;
-        const int par_bonds = __popc(e0) + __popc(e1) + (D == 3 ? __popc(e2) : 0);
-        m_acc += 2 * __popc(eq_bits(rb.a, ones) & vmask) - nvalid;
-        e_acc -= 2 * par_bonds - D * nvalid;
-      } else if (MM == 2) {
-        // E = number of unequal +d bonds; histogram n[k] of the states
-        const int par_bonds = __popc(e0) + __popc(e1) + (D == 3 ? __popc(e2) : 0);
-        e_acc += D * nvalid - par_bonds;
-        if (lat.q <= kSmallQ) {
-          for (int k = 0; k < lat.q; ++k) {
-            uint32_t kk[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) kk[j] = 0x01010101u * (uint32_t)k;
-            const unsigned c = (unsigned)__popc(eq_bits(rb.a, kk) & vmask);
-            if (c) atomicAdd(&s_whist[warp * kSmallQ + k], c);
-          }
-        } else {
-#pragma unroll
-          for (int b = 0; b < 32; ++b)
-            if (b < nvalid) atomicAdd(&s_hist[(rb.a[b >> 2] >> (8 * (b & 3))) & 0xffu], 1u);
-        }
-      }
+      if (MM != 0) measure_row<D, MM>(rb, e0, e1, e2, vmask, nvalid, lat.q, m_acc, e_acc, s_whist + warp * kSmallQ, s_hist);
       A0 = e0 ? (e0 & bernoulli_word(g, sweep, 0, lat.t_bond, e0, lat.rk)) : 0u;
       A1 = e1 ? (e1 & bernoulli_word(g, sweep, 1, lat.t_bond, e1, lat.rk)) : 0u;
       if (D == 3) A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, e2, lat.rk)) : 0u;
@@ -348,6 +357,49 @@ __global__ void __launch_bounds__(S::THREADS, label_blocks(S::THREADS, LAYOUT))
   if (step == 0u && !m.measure0) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
   else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
   else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
+}
+
+// Stand-alone measurement of an Ising (MM 1) or Potts (MM 2) state: a
+// thread per 32-site row word (grid-stride), the labeling kernel's row loads
+// and equality masks, sums added to the measurement slots by block.
+template <int D, int MM>
+__global__ void __launch_bounds__(256) k_measure_rows(const __grid_constant__ Lattice lat, const Measure mb) {
+  constexpr int NW = 256 / 32;
+  __shared__ unsigned int s_hist[MM == 2 ? 256 : 1];
+  __shared__ unsigned int s_whist[MM == 2 ? NW * kSmallQ : 1];
+  __shared__ long long s_red[NW];
+  const int warp = threadIdx.x >> 5;
+  if (MM == 2) {
+    for (int k = threadIdx.x; k < 256; k += 256) s_hist[k] = 0u;
+    for (int k = threadIdx.x; k < NW * kSmallQ; k += 256) s_whist[k] = 0u;
+    __syncthreads();
+  }
+  const int L = lat.L;
+  const uint32_t words = lat.R * (uint32_t)lat.W;
+  int m_acc = 0, e_acc = 0;
+  for (uint32_t g = blockIdx.x * 256u + threadIdx.x; g < words; g += gridDim.x * 256u) {
+    const uint32_t row = g / (uint32_t)lat.W, tx = g % (uint32_t)lat.W;
+    const int x0 = 32 * (int)tx;
+    const int nvalid = min(32, L - x0);
+    const uint32_t vmask = (nvalid >= 32) ? kFull : ((1u << nvalid) - 1u);
+    const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
+    const uint32_t y1 = (y + 1u == (uint32_t)L) ? 0u : y + 1u;
+    const uint32_t z1 = (D == 3) ? ((z + 1u == (uint32_t)L) ? 0u : z + 1u) : 0u;
+    RowBytes rb;
+    load_rows<D>(static_cast<const uint8_t*>(lat.spins), L, x0, row, y1 + (uint32_t)L * z, y + (uint32_t)L * z1, rb);
+    const uint32_t e0 = eq_bits(rb.a, rb.ax) & vmask;
+    const uint32_t e1 = eq_bits(rb.a, rb.ay) & vmask;
+    const uint32_t e2 = (D == 3) ? (eq_bits(rb.a, rb.az) & vmask) : 0u;
+    measure_row<D, MM>(rb, e0, e1, e2, vmask, nvalid, lat.q, m_acc, e_acc, s_whist + warp * kSmallQ, s_hist);
+  }
+  if (MM == 2) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < kSmallQ; k += 256)
+      for (int w = 0; w < NW; ++w) s_hist[k] += s_whist[w * kSmallQ + k];
+    __syncthreads();
+    add_histogram(lat, mb, blockIdx.x, s_hist);
+  }
+  add_integer_sums<NW>(mb, blockIdx.x, (long long)m_acc, (long long)e_acc, s_red);
 }
 
 // ---------------------------------------------------------------- XY bonds
@@ -610,6 +662,22 @@ cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int sche
   static_assert(kTileShapes == 3, "one instantiation per shape");
   if (dim == 2) return label_batch_dim<2>(bv, shape, schedule, ising_tiles, potts_tiles, st);
   return label_batch_dim<3>(bv, shape, schedule, ising_tiles, potts_tiles, st);
+}
+
+cudaError_t launch_measure_rows(const Lattice& lat, const Measure& m, cudaStream_t st) {
+  const uint32_t words = lat.R * (uint32_t)lat.W;
+  unsigned g = (words + 255u) / 256u;
+  if (g > (unsigned)kMeasureBlocks) g = (unsigned)kMeasureBlocks;
+  if (g == 0) g = 1;
+  const bool potts = lat.model == kPotts;
+  if (lat.dim == 2) {
+    if (potts) k_measure_rows<2, 2><<<g, 256, 0, st>>>(lat, m);
+    else k_measure_rows<2, 1><<<g, 256, 0, st>>>(lat, m);
+  } else {
+    if (potts) k_measure_rows<3, 2><<<g, 256, 0, st>>>(lat, m);
+    else k_measure_rows<3, 1><<<g, 256, 0, st>>>(lat, m);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Measure& m,

@@ -2,10 +2,10 @@
 // magnetization M, the energy of the Hamiltonian, the Potts M^2 equation;
 // Sec. 3: the moments entering U = <M^4>/<M^2>^2).
 //
-// k_measure: one warp per lattice row (grid-stride), lane per site;
-//   integer M / E / Potts histogram (warp-aggregated shared atomics) or the
+// k_measure: one warp per lattice row (grid-stride), lane per site; the
 //   clock model's fixed-point cos / sin sums added to the measurement
-//   slots, or float XY per-block partials.
+//   slots, or float XY per-block partials (Ising/Potts states are measured
+//   by a thread per row word, k_measure_rows in sw_label.cu).
 // k_finalize: one block sums slots / partials in a fixed order, writes the
 //   sweep record and adds M2, M2^2, E, E^2 and the cluster count to the FP64
 //   accumulators (explicit round-to-nearest operations, no contraction).
@@ -34,16 +34,13 @@ __global__ void __launch_bounds__(256) k_init(const __grid_constant__ Lattice la
 
 constexpr int kMThreads = 256, kMWarps = kMThreads / 32;
 
+// XY and clock states (Ising/Potts: k_measure_rows in sw_label.cu).
 template <int MODEL, int D>
 __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t sweep, Measure mb) {
-  __shared__ unsigned int s_hist[256];
+  static_assert(MODEL == kXY || MODEL == kClock, "row-word kernel for Ising/Potts");
   __shared__ long long s_ri[kMWarps];
   __shared__ double s_rd[kMWarps];
   const int L = lat.L, lane = threadIdx.x & 31;
-  if (MODEL == kPotts) {
-    for (int k = threadIdx.x; k < lat.q; k += blockDim.x) s_hist[k] = 0u;
-    __syncthreads();
-  }
   long long m = 0, e = 0, cb = 0;
   float fx = 0.f, fy = 0.f, fe = 0.f;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -61,22 +58,7 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
       jn[0] = (x + 1 == L) ? rowL : i + 1u;
       jn[1] = i + dy;
       jn[2] = i + dz;
-      if (MODEL == kIsing) {
-        const int8_t* s = static_cast<const int8_t*>(lat.spins);
-        const int si = s[i];
-        int nb = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) nb += s[jn[d]];
-        m += si;
-        e -= si * nb;
-      } else if (MODEL == kPotts) {
-        const uint8_t* s = static_cast<const uint8_t*>(lat.spins);
-        const uint32_t si = s[i];
-#pragma unroll
-        for (int d = 0; d < D; ++d) e += (s[jn[d]] != si) ? 1 : 0;
-        const unsigned grp = __match_any_sync(__activemask(), si);
-        if (lane == __ffs(grp) - 1) atomicAdd(&s_hist[si], (unsigned)__popc(grp));
-      } else if (MODEL == kClock) {
+      if (MODEL == kClock) {
         // fixed-point sums: C[p_i], S[p_i] and C[(p_i - p_j) mod q]
         const uint16_t* sp = static_cast<const uint16_t*>(lat.spins);
         const int q = lat.q;
@@ -97,16 +79,8 @@ __global__ void __launch_bounds__(kMThreads) k_measure(Lattice lat, uint32_t swe
       }
     }
   }
-  if (MODEL == kPotts) {
-    __syncthreads();
-    add_histogram(lat, mb, blockIdx.x, s_hist);
-  }
   if (MODEL == kClock) {
     add_clock_sums<kMWarps>(mb, blockIdx.x, m, e, cb, s_ri);
-    return;
-  }
-  if (MODEL != kXY) {
-    add_integer_sums<kMWarps>(mb, blockIdx.x, m, e, s_ri);
     return;
   }
   // XY: float within a warp, double across warps; per-block partials are
@@ -147,15 +121,14 @@ cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st) {
 cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const Measure& m,
                            cudaStream_t st) {
   const unsigned g = grid_for(lat.R, kMeasureBlocks);
-  if (lat.dim == 2) {
-    if (model == kIsing) k_measure<kIsing, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
-    else if (model == kPotts) k_measure<kPotts, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
-    else if (model == kClock) k_measure<kClock, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
+  if (model == kIsing || model == kPotts) {
+    const cudaError_t e = launch_measure_rows(lat, m, st);
+    if (e != cudaSuccess) return e;
+  } else if (lat.dim == 2) {
+    if (model == kClock) k_measure<kClock, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else k_measure<kXY, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
   } else {
-    if (model == kIsing) k_measure<kIsing, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
-    else if (model == kPotts) k_measure<kPotts, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
-    else if (model == kClock) k_measure<kClock, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
+    if (model == kClock) k_measure<kClock, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else k_measure<kXY, 3><<<g, kMThreads, 0, st>>>(lat, sweep, m);
   }
   Measure mf = m;
