@@ -337,8 +337,7 @@ int batch_sweep(sw_batch* b, int n, float* ms) {
     b->h_members[m].meas = h->meas;
     b->h_members[m].sweep0 = (uint32_t)h->sweep;
     b->h_members[m].nsweeps = count[m];
-    b->h_members[m].measure0 = measure0 ? 1u : 0u;
-    if (measure0) h->pending = 0;  // written by the batch
+    b->h_members[m].measure0 = measure0 ? 1u : 0u;  // pending is replaced once the replays are enqueued
   }
   if (e != cudaSuccess) return bcuda(e, "batch ordering");
   if ((e = cudaMemcpyAsync(b->d_members, b->h_members, b->members.size() * sizeof(BatchMember),
