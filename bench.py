@@ -56,7 +56,7 @@ PHASES = ["bond_label", "merge", "flip", "measure"]
 # DRAM bytes (read + write) of one launch of the dominant kernel, k_label
 # with measurement, from one ncu capture of this build (cold cache; see
 # profiles/sweep_kernels_ising3d_L256.md); None once that kernel changes.
-KERNEL_DRAM_BYTES = {"bond_label": 16.847360e6 + 12.758272e6}
+KERNEL_DRAM_BYTES = {"bond_label": 16.847104e6 + 12.827648e6}
 # kernels one measured sweep launches: k_label (bonds + tile labels + the
 # previous sweep's measurement), k_merge, k_compress, k_apply
 KERNELS_PER_SWEEP = 4
