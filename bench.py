@@ -438,12 +438,13 @@ def _job_list(specs):
 def batch_launches(specs, schedule):
     """Kernels one batch sweep launches: the tiled members' labels (one
     launch per model under schedule 0, one in all under schedule 1), merge,
-    compression and apply; one launch per model of the small members (at
-    most 8192 sites in 2D, 4096 in 3D); the step counter."""
-    def is_small(d, L):
-        return L ** d <= (8192 if d == 2 else 4096)
-    tiled = {m for (m, d, L, _, _, _) in specs if not is_small(d, L)}
-    small = {m for (m, d, L, _, _, _) in specs if is_small(d, L)}
+    compression and apply; one launch per model of the small members (2D
+    Ising up to 4096 sites, 2D Potts up to 8192, 3D up to 1024); the step
+    counter."""
+    def is_small(m, d, L):
+        return L ** d <= ((8192 if m == 1 else 4096) if d == 2 else 1024)
+    tiled = {m for (m, d, L, _, _, _) in specs if not is_small(m, d, L)}
+    small = {m for (m, d, L, _, _, _) in specs if is_small(m, d, L)}
     labels = (len(tiled) if schedule == 0 else 1) if tiled else 0
     return labels + (3 if tiled else 0) + len(small) + 1
 

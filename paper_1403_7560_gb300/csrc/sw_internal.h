@@ -201,8 +201,11 @@ size_t handle_block_bytes();
 // Small Ising/Potts lattices (sw_small.cu): whole sweeps by one CTA with
 // the lattice in shared memory, n sweeps per launch, records written as
 // the tiled path writes them.
-constexpr int kSmallSites = 8192;
+constexpr int kSmallSites = 8192;  // the shared-memory layout's capacity
 size_t small_layout_bytes_max();
+// Largest lattice (sites) that takes the one-CTA path: 2D Ising 4096, 2D
+// Potts 8192, 3D 1024 (where it beats the tiled path).
+uint32_t small_sites_limit(int model, int dim);
 bool small_lattice(const Lattice& lat);
 cudaError_t launch_sweeps_small(const Lattice& lat, const Measure& m, uint32_t sweep0, int n, bool measure,
                                 cudaStream_t st);
