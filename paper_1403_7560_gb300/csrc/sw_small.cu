@@ -1,5 +1,6 @@
-// Small Ising/Potts lattices (N <= kSmallSites): whole sweeps by one CTA
-// with the lattice in shared memory, n sweeps per launch.
+// Small Ising/Potts lattices (N <= small_sites_limit: 2D Ising 4096, 2D
+// Potts 8192, 3D 1024): whole sweeps by one CTA with the lattice in shared
+// memory, n sweeps per launch.
 //
 // The tiled path pays four kernel launches and a global merge per sweep,
 // which for a lattice of a few thousand sites is nearly all of the time.
