@@ -192,6 +192,23 @@ def cpu_baseline(sweeps: int = 4, warm: int = 1):
                       f"from the seeded start; {dt:.1f} s on one host core"}
 
 
+def cpu_baseline_xy(sweeps: int = 2, warm: int = 1):
+    """The oracle on the 3D XY L=256 workload (seed 1002), single-threaded:
+    `sweeps` measured sweeps after `warm` untimed ones."""
+    import oracle
+    name, model, dim, L_, q, T_, seed, _, _ = OTHER_WORKLOADS[0]
+    o = oracle.Oracle(model, dim, L_, q, T_, seed)
+    o.sweep(warm)
+    t0 = time.perf_counter()
+    o.sweep(sweeps)
+    dt = time.perf_counter() - t0
+    o.close()
+    n = L_ ** dim
+    return {"value": n * sweeps / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} measured sweeps of the full {name} lattice after {warm} untimed sweep(s); "
+                      f"{dt:.1f} s on one host core"}
+
+
 def run_reference(args):
     # the oracle runs once, on rank 0; other ranks have nothing to do
     if int(os.environ.get("RANK", "0")) != 0:
@@ -225,6 +242,10 @@ OTHER_WORKLOADS = [
     ("clock3d_q512_L256", 3, 3, 256, 512, 1.0 / 0.4541652, 1002, 20, 50),
     ("ising2d_L4096", 0, 2, 4096, 2, 2.269185, 1000, 20, 50),
 ]
+# reference bytes per site per sweep of the other workloads (3D XY: angle
+# in + mask out, mask in + label out, label in + angle in + angle out;
+# 2D Ising: spin in + 2/8 mask out, mask in + label out, label in + spin out)
+B_REF_OTHER = {"xy3d_L256": 20.75, "ising2d_L4096": 10.5}
 # the 2D Ising L=64 configuration as specified: 200 discarded, then 1000
 # measured sweeps in one sw_sweep call (events around the call)
 SMALL_WORKLOAD = ("ising2d_L64", 0, 2, 64, 2, 2.269185, 1000, 200, 1000)
@@ -255,6 +276,10 @@ def other_workloads(sw, stream, flush, rank):
         n = L_ ** dim
         out[name] = {"value": n / (ms * 1e6), "unit": UNIT, "ms_per_step": ms, "ns_per_site": ms * 1e6 / n,
                      "steps": steps, "sites": n, "T": T_, "e_per_spin": mom["e_per_spin"]}
+        if name in B_REF_OTHER:
+            # the reference bytes model of this workload against the measured copy bandwidth
+            gbps = out[name]["value"] * B_REF_OTHER[name]
+            out[name]["b_ref"] = {"bytes_per_site": B_REF_OTHER[name], "GBps": gbps, "frac": gbps / peaks()[0]}
         sw.sw_destroy(h)
     name, model, dim, L_, q, T_, seed, discard, steps = SMALL_WORKLOAD
     h = sw.sw_create(model, dim, L_, q, T_, seed + rank)
@@ -423,6 +448,7 @@ def run_gpu(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sweeps)
+            line["other_workloads"]["xy3d_L256"]["cpu_baseline"] = cpu_baseline_xy()
         print(json.dumps(line), flush=True)
     sw.sw_destroy(h)
     if world > 1:
