@@ -198,6 +198,8 @@ cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], h->stream);
   if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], h->stream);
+  // the flip writes the spins: a download's snapshot of them goes first
+  if (e == cudaSuccess) e = swgb::guard_state_write(h, h->lat.spins, h->stream);
   if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas, measure, finalize, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->stream);
   if (e == cudaSuccess && measure) {
@@ -214,6 +216,7 @@ int run_sweeps(sw_handle* h, int n, bool measure) {
     // the whole lattice in one CTA's shared memory, many sweeps per launch
     if (h->sweep + (uint64_t)n >= 0xffffffffull) return fail(SW_ERR_BAD_ARG, "sweep counter exhausted");
     cudaError_t e = flush_pending(h);
+    if (e == cudaSuccess) e = swgb::guard_state_write(h, h->lat.spins, h->stream);
     for (int done = 0; e == cudaSuccess && done < n;) {
       const int chunk = n - done < 256 ? n - done : 256;
       e = swgb::launch_sweeps_small(h->lat, h->meas, (uint32_t)h->sweep, chunk, measure, h->stream);
@@ -461,6 +464,7 @@ int sw_set_spins(sw_handle* h, const void* host, size_t bytes) {
   if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
   if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
   cudaError_t e = flush_pending(h);
+  if (e == cudaSuccess) e = swgb::guard_state_write(h, h->lat.spins, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->lat.spins, host, bytes, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_spins");
   return check_device_error(h);
@@ -477,6 +481,7 @@ int sw_set_spins_device(sw_handle* h, const void* dev, size_t bytes) {
   if (!h || !dev) return fail(SW_ERR_BAD_ARG, "NULL argument");
   if (bytes != h->spin_bytes) return fail(SW_ERR_BAD_ARG, "bytes != sw_spin_bytes");
   cudaError_t e = flush_pending(h);
+  if (e == cudaSuccess) e = swgb::guard_state_write(h, h->lat.spins, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->lat.spins, dev, bytes, cudaMemcpyDeviceToDevice, h->stream);
   return e == cudaSuccess ? SW_OK : cuda_fail(e, "set_spins_device");
 }

@@ -5,18 +5,19 @@
 // off the sweep's critical path.  Uploads run on their own stream into a
 // staging buffer that is swapped with the state buffer once the upload is
 // done (kernels launched afterwards read the new state); downloads copy the
-// state into a snapshot buffer on the compute stream (a copy kernel) and
-// from there to the host on a second stream, so the next sweep
-// may overwrite the state while the download runs.  Events order the three
-// streams:
+// state into a snapshot buffer and from there to the host, both on a second
+// stream, so the sweeps go on while the download runs.  Events order the
+// three streams:
 //   upload k:   io_in waits ev_in_free (the buffer it fills is no longer
-//               read), copies, records ev_in_done; the compute stream waits
-//               ev_in_done, the buffers are swapped, ev_in_free is recorded.
-//   download k: the compute stream waits ev_out_done (the snapshot is no
-//               longer read), copies the state to the snapshot with a copy
-//               kernel (so no copy engine is shared with the downloads),
-//               records ev_snap; io_out waits ev_snap, copies, records
-//               ev_out_done.
+//               read) and, if the buffer was snapshotted since its last
+//               write, that snapshot; copies, records ev_in_done; the
+//               compute stream waits ev_in_done, the buffers are swapped,
+//               ev_in_free is recorded.
+//   download k: the compute stream records ev_state (the state is final);
+//               io_out waits for it, copies the state to the snapshot
+//               (device to device), records ev_snap of that buffer, copies
+//               the snapshot to the host.  The next write of the buffer, on
+//               any stream, first waits for ev_snap (guard_state_write).
 //   record:     the compute stream records ev_rec once the record is final;
 //               io_out waits ev_rec and copies it (small copies issued on
 //               the compute stream would queue behind a download on the
@@ -28,15 +29,6 @@
 #include "sw_internal.h"
 
 namespace {
-
-// 16-byte words, then the remaining bytes (buffers from cudaMalloc, so both
-// start 256-byte aligned).
-__global__ void __launch_bounds__(256) k_copy(uint4* dst, const uint4* src, size_t n16, uint8_t* dst1,
-                                              const uint8_t* src1, size_t n1) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = __ldcs(&src[i]);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride) dst1[i] = src1[i];
-}
 
 int io_fail(int code, const std::string& msg) {
   swgb::set_last_error(msg);
@@ -53,13 +45,16 @@ cudaError_t ensure_io(sw_handle* h) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, h->spin_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->snap, h->spin_bytes);
-  cudaEvent_t* evs[5] = {&h->ev_in_done, &h->ev_in_free, &h->ev_snap, &h->ev_out_done, &h->ev_rec};
+  cudaEvent_t* evs[6] = {&h->ev_in_done, &h->ev_in_free, &h->ev_state, &h->ev_rec, &h->ev_snap[0], &h->ev_snap[1]};
   for (cudaEvent_t* ev : evs)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
     swgb::release_io(h);
+    return e;
   }
+  h->io_buf[0] = h->lat.spins;
+  h->io_buf[1] = h->stage_in;
   return e;
 }
 
@@ -72,38 +67,41 @@ int check_io_args(sw_handle* h, const void* host, size_t bytes) {
 
 }  // namespace
 
-cudaError_t swgb::launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
-  const size_t n16 = bytes / 16, tail = bytes % 16;
-  size_t g = (n16 + 255) / 256;
-  if (g > 152u * 8u) g = 152u * 8u;
-  if (g == 0) g = 1;
-  k_copy<<<(unsigned)g, 256, 0, st>>>(static_cast<uint4*>(dst), static_cast<const uint4*>(src), n16,
-                                      static_cast<uint8_t*>(dst) + 16 * n16,
-                                      static_cast<const uint8_t*>(src) + 16 * n16, tail);
-  return cudaGetLastError();
+cudaError_t swgb::guard_state_write(sw_handle* h, const void* buf, cudaStream_t st) {
+  for (int i = 0; i < 2; ++i) {
+    if (!h->snap_wait[i] || buf != h->io_buf[i]) continue;
+    // later writes of the buffer are ordered after this one: on st itself,
+    // or on the other stream through the upload/swap events
+    h->snap_wait[i] = false;
+    return cudaStreamWaitEvent(st, h->ev_snap[i], 0);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t swgb::wait_io(sw_handle* h) {
   cudaError_t e = cudaSuccess;
   if (h->io_in) e = cudaStreamSynchronize(h->io_in);
   if (e == cudaSuccess && h->io_out) e = cudaStreamSynchronize(h->io_out);
+  if (e == cudaSuccess) h->snap_wait[0] = h->snap_wait[1] = false;
   return e;
 }
 
 void swgb::release_io(sw_handle* h) {
   if (h->io_in) cudaStreamSynchronize(h->io_in);
   if (h->io_out) cudaStreamSynchronize(h->io_out);
-  cudaEvent_t evs[5] = {h->ev_in_done, h->ev_in_free, h->ev_snap, h->ev_out_done, h->ev_rec};
+  cudaEvent_t evs[6] = {h->ev_in_done, h->ev_in_free, h->ev_state, h->ev_rec, h->ev_snap[0], h->ev_snap[1]};
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
-  h->ev_in_done = h->ev_in_free = h->ev_snap = h->ev_out_done = h->ev_rec = nullptr;
+  h->ev_in_done = h->ev_in_free = h->ev_state = h->ev_rec = h->ev_snap[0] = h->ev_snap[1] = nullptr;
   cudaFree(h->stage_in);
   cudaFree(h->snap);
   h->stage_in = h->snap = nullptr;
+  h->io_buf[0] = h->io_buf[1] = nullptr;
+  h->snap_wait[0] = h->snap_wait[1] = false;
   if (h->io_in) cudaStreamDestroy(h->io_in);
   if (h->io_out) cudaStreamDestroy(h->io_out);
   h->io_in = h->io_out = nullptr;
-  h->in_free_set = h->out_done_set = false;
+  h->in_free_set = false;
 }
 
 extern "C" {
@@ -116,6 +114,7 @@ int sw_set_spins_async(sw_handle* h, const void* host, size_t bytes) {
   // the pending measurement reads the state being replaced
   e = swgb::flush_pending(h);
   if (e == cudaSuccess && h->in_free_set) e = cudaStreamWaitEvent(h->io_in, h->ev_in_free, 0);
+  if (e == cudaSuccess) e = swgb::guard_state_write(h, h->stage_in, h->io_in);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->stage_in, host, bytes, cudaMemcpyHostToDevice, h->io_in);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_in_done, h->io_in);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_in_done, 0);
@@ -132,14 +131,15 @@ int sw_get_spins_async(sw_handle* h, void* host, size_t bytes) {
   if (rc != SW_OK) return rc;
   cudaError_t e = ensure_io(h);
   if (e != cudaSuccess) return io_cuda(e, "asynchronous I/O setup");
-  if (h->out_done_set) e = cudaStreamWaitEvent(h->stream, h->ev_out_done, 0);
-  if (e == cudaSuccess) e = swgb::launch_copy(h->snap, h->lat.spins, bytes, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_snap, h->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_snap, 0);
+  const int b = h->lat.spins == h->io_buf[0] ? 0 : 1;
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_state, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_state, 0);
+  // the previous download's host copy precedes this snapshot on io_out
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->snap, h->lat.spins, bytes, cudaMemcpyDeviceToDevice, h->io_out);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_snap[b], h->io_out);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, h->snap, bytes, cudaMemcpyDeviceToHost, h->io_out);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_out_done, h->io_out);
   if (e != cudaSuccess) return io_cuda(e, "get_spins_async");
-  h->out_done_set = true;
+  h->snap_wait[b] = true;
   return SW_OK;
 }
 

@@ -103,6 +103,42 @@ def test_downloads_overlap_later_sweeps(sw):
         sw.sw_destroy(h)
 
 
+@pytest.mark.parametrize("dim,L", [(3, 32), (2, 32)], ids=["tiled", "one_cta"])
+def test_download_snapshots_with_uploads_in_between(sw, dim, L):
+    """Downloads interleaved with uploads that swap the two state buffers:
+    each download holds the state at its enqueue point, and an upload into a
+    buffer still being downloaded waits for that download."""
+    N = L ** dim
+    rng = np.random.default_rng(77)
+    states = [pinned(N, np.int8) for _ in range(3)]
+    for st in states:
+        st[:] = rng.choice(np.array([-1, 1], dtype=np.int8), N)
+    outs = [pinned(N, np.int8) for _ in range(3)]
+    h = sw.sw_create(ISING, dim, L, 2, 2.3 if dim == 2 else 4.4, 9)
+    ref = sw.sw_create(ISING, dim, L, 2, 2.3 if dim == 2 else 4.4, 9)
+    try:
+        sw.sw_sweep(h, 1)
+        want0 = sw.sw_get_spins(h)
+        sw.sw_get_spins_async(h, outs[0])     # buffer A
+        sw.sw_set_spins_async(h, states[0])   # into B, swapped in
+        sw.sw_get_spins_async(h, outs[1])     # buffer B
+        sw.sw_set_spins_async(h, states[1])   # into A, after download 0
+        sw.sw_sweep(h, 1)                     # writes A
+        sw.sw_get_spins_async(h, outs[2])     # buffer A after the sweep
+        sw.sw_set_spins_async(h, states[2])   # into B, after download 1
+        sw.sw_wait_io(h)
+        sw.sw_sweep(ref, 1)
+        sw.sw_set_spins(ref, states[1])
+        sw.sw_sweep(ref, 1)
+        assert np.array_equal(outs[0], want0)
+        assert np.array_equal(outs[1], states[0])
+        assert np.array_equal(outs[2], sw.sw_get_spins(ref))
+        assert np.array_equal(sw.sw_get_spins(h), states[2])
+    finally:
+        sw.sw_destroy(h)
+        sw.sw_destroy(ref)
+
+
 def test_errors(sw):
     h = sw.sw_create(ISING, 2, 32, 2, 2.0, 1)
     b = sw.sw_batch_create(2)
