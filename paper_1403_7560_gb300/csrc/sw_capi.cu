@@ -43,12 +43,13 @@ namespace {
 // flag, accumulators, cluster counts [2][kSlots], slot sums [kSlots][2],
 // slot histograms [kSlots][256], XY partials, series ring.
 struct BlockLayout {
-  size_t err, acc, ncl, sums, hist, pd, series, total;
+  size_t err, done, acc, ncl, sums, hist, pd, series, total;
 };
 
 BlockLayout block_layout() {
   BlockLayout b;
   b.err = 0;
+  b.done = 8;
   b.acc = 64;
   b.ncl = 128;
   b.sums = b.ncl + 2 * 8 * (size_t)swgb::kSlots;
@@ -312,6 +313,7 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   h->meas.acc = reinterpret_cast<double*>(blk + off_acc);
   h->meas.part_d = reinterpret_cast<double*>(blk + off_pd);
   h->meas.xy_blocks = 0;
+  h->meas.done = reinterpret_cast<unsigned int*>(blk + bl.done);
   h->meas.series = blk + off_series;
   h->meas.series_cap = kSeriesCap;
 

@@ -61,6 +61,7 @@ struct Measure {
   unsigned long long* csums;      // clock: [kSlots][3] integer sums of C[p_i], S[p_i], C[p_i - p_j]
   const long long* cfix;          // clock: C[p] = round(2^30 cos(2 pi p / q)) [q], then S [q]
   int xy_blocks;                  // blocks that wrote part_d
+  unsigned int* done;             // blocks of a stand-alone measurement that have added their sums
   double* acc;                    // n, sum M2, M4, E, E2, nclusters
   void* series;                   // sw_record ring
   int series_cap;
@@ -168,9 +169,9 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
 // (sums, then a one-block finalisation).
 cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const Measure& m,
                            cudaStream_t st);
-// The sums of the stand-alone Ising/Potts measurement (a thread per row
-// word, sw_label.cu); launch_measure adds the finalisation.
-cudaError_t launch_measure_rows(const Lattice& lat, const Measure& m, cudaStream_t st);
+// Stand-alone Ising/Potts measurement as the record of `sweep` (a thread per
+// row word, sw_label.cu); the last block to finish writes the record.
+cudaError_t launch_measure_rows(const Lattice& lat, uint32_t sweep, const Measure& m, cudaStream_t st);
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);
 
 // Batched phases: one launch over every tile of every member (Ising/Potts,

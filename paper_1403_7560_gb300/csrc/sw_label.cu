@@ -359,15 +359,20 @@ __global__ void __launch_bounds__(S::THREADS, label_blocks(S::THREADS, LAYOUT))
   else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
 }
 
-// Stand-alone measurement of an Ising (MM 1) or Potts (MM 2) state: a
-// thread per 32-site row word (grid-stride), the labeling kernel's row loads
-// and equality masks, sums added to the measurement slots by block.
+// Stand-alone measurement of an Ising (MM 1) or Potts (MM 2) state as the
+// record of `sweep`: a thread per 32-site row word (grid-stride), the
+// labeling kernel's row loads and equality masks, sums added to the
+// measurement slots by block; the last block to finish (a counter) writes
+// the record and the FP64 accumulators from the complete slots.
 template <int D, int MM>
-__global__ void __launch_bounds__(256) k_measure_rows(const __grid_constant__ Lattice lat, const Measure mb) {
+__global__ void __launch_bounds__(256) k_measure_rows(const __grid_constant__ Lattice lat,
+                                                      const __grid_constant__ Measure mb, uint32_t sweep) {
   constexpr int NW = 256 / 32;
   __shared__ unsigned int s_hist[MM == 2 ? 256 : 1];
   __shared__ unsigned int s_whist[MM == 2 ? NW * kSmallQ : 1];
   __shared__ long long s_red[NW];
+  __shared__ double s_rd[NW];
+  __shared__ bool s_last;
   const int warp = threadIdx.x >> 5;
   if (MM == 2) {
     for (int k = threadIdx.x; k < 256; k += 256) s_hist[k] = 0u;
@@ -400,6 +405,15 @@ __global__ void __launch_bounds__(256) k_measure_rows(const __grid_constant__ La
     add_histogram(lat, mb, blockIdx.x, s_hist);
   }
   add_integer_sums<NW>(mb, blockIdx.x, (long long)m_acc, (long long)e_acc, s_red);
+  // this block's slot additions are visible before it counts itself done
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(mb.done, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  finalize_record<NW>(lat, mb, sweep, s_red, s_rd);
+  if (threadIdx.x == 0) *mb.done = 0u;
 }
 
 // ---------------------------------------------------------------- XY bonds
@@ -664,18 +678,18 @@ cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int sche
   return label_batch_dim<3>(bv, shape, schedule, ising_tiles, potts_tiles, st);
 }
 
-cudaError_t launch_measure_rows(const Lattice& lat, const Measure& m, cudaStream_t st) {
+cudaError_t launch_measure_rows(const Lattice& lat, uint32_t sweep, const Measure& m, cudaStream_t st) {
   const uint32_t words = lat.R * (uint32_t)lat.W;
   unsigned g = (words + 255u) / 256u;
   if (g > (unsigned)kMeasureBlocks) g = (unsigned)kMeasureBlocks;
   if (g == 0) g = 1;
   const bool potts = lat.model == kPotts;
   if (lat.dim == 2) {
-    if (potts) k_measure_rows<2, 2><<<g, 256, 0, st>>>(lat, m);
-    else k_measure_rows<2, 1><<<g, 256, 0, st>>>(lat, m);
+    if (potts) k_measure_rows<2, 2><<<g, 256, 0, st>>>(lat, m, sweep);
+    else k_measure_rows<2, 1><<<g, 256, 0, st>>>(lat, m, sweep);
   } else {
-    if (potts) k_measure_rows<3, 2><<<g, 256, 0, st>>>(lat, m);
-    else k_measure_rows<3, 1><<<g, 256, 0, st>>>(lat, m);
+    if (potts) k_measure_rows<3, 2><<<g, 256, 0, st>>>(lat, m, sweep);
+    else k_measure_rows<3, 1><<<g, 256, 0, st>>>(lat, m, sweep);
   }
   return cudaGetLastError();
 }

@@ -121,10 +121,8 @@ cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st) {
 cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const Measure& m,
                            cudaStream_t st) {
   const unsigned g = grid_for(lat.R, kMeasureBlocks);
-  if (model == kIsing || model == kPotts) {
-    const cudaError_t e = launch_measure_rows(lat, m, st);
-    if (e != cudaSuccess) return e;
-  } else if (lat.dim == 2) {
+  if (model == kIsing || model == kPotts) return launch_measure_rows(lat, sweep, m, st);  // finalises itself
+  if (lat.dim == 2) {
     if (model == kClock) k_measure<kClock, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
     else k_measure<kXY, 2><<<g, kMThreads, 0, st>>>(lat, sweep, m);
   } else {
