@@ -6,8 +6,8 @@
 //   clock model's fixed-point cos / sin sums added to the measurement
 //   slots, or float XY per-block partials (Ising/Potts states are measured
 //   by a thread per row word, k_measure_rows in sw_label.cu).
-// k_finalize: one block sums slots / partials in a fixed order, writes the
-//   sweep record and adds M2, M2^2, E, E^2 and the cluster count to the FP64
+// k_finalize (after k_measure): one block sums slots / partials in a fixed
+//   order, writes the sweep record and adds M2, M2^2, E, E^2 and the cluster count to the FP64
 //   accumulators (explicit round-to-nearest operations, no contraction).
 #include "sw_device.cuh"
 
