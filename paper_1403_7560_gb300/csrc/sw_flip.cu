@@ -213,10 +213,16 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
   long long roots = 0;
   for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < lat.N; base += kFlipUnroll * stride) {
     uint32_t v[kFlipUnroll];
+    // XY and clock: the old state (angle bits / clock state) is loaded beside
+    // the forest word instead of after the root's word (a shorter load chain)
+    uint32_t old[kFlipUnroll];
 #pragma unroll
     for (int k = 0; k < kFlipUnroll; ++k) {
       const uint32_t i = base + k * stride;
       v[k] = (i < lat.N) ? __ldcg(&lat.forest[i]) : lr_bit;
+      old[k] = 0u;
+      if (MODEL == kXY && i < lat.N) old[k] = __float_as_uint(__ldcg(&static_cast<const float*>(lat.spins)[i]));
+      if (MODEL == kClock && i < lat.N) old[k] = __ldcg(&static_cast<const uint16_t*>(lat.spins)[i]);
     }
 #pragma unroll
     for (int k = 0; k < kFlipUnroll; ++k) {
@@ -237,13 +243,13 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
         if (draw) {
           uint16_t* sp = static_cast<uint16_t*>(lat.spins);
           const int q = lat.q;
-          sp[i] = (uint16_t)wrap_mod((int)s_mirror - clock_state(sp[i], q), q);
+          sp[i] = (uint16_t)wrap_mod((int)s_mirror - clock_state(old[k], q), q);
         }
       } else if (draw) {
         float* th = static_cast<float*>(lat.spins);
         const float phi = s_phi;
         const float two_pi = 0x1.921fb6p+2f, pi = 0x1.921fb6p+1f;
-        float t = __fsub_rn(__fadd_rn(__fmul_rn(2.0f, phi), pi), th[i]);
+        float t = __fsub_rn(__fadd_rn(__fmul_rn(2.0f, phi), pi), __uint_as_float(old[k]));
         if (t >= two_pi) t = __fsub_rn(t, two_pi);
         if (t >= two_pi) t = __fsub_rn(t, two_pi);
         if (t < 0.0f) t = __fadd_rn(t, two_pi);
