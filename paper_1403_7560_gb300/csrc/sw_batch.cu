@@ -452,7 +452,8 @@ size_t sw_device_bytes(int model, int dim, int L, int q) {
   size_t ntiles = 0, hook_words = 0;
   swgb::tile_buffers(model, dim, L, &ntiles, &hook_words);
   const size_t spins = N * (model == SW_XY ? 4 : model == SW_CLOCK ? 2 : 1);
-  const size_t clock = (model == SW_CLOCK) ? (size_t)4 * q * q * 4 + (size_t)2 * q * 8 + 3 * swgb::kSlots * 8 : 0;
+  const size_t clock =
+      (model == SW_CLOCK) ? (size_t)4 * q * q * 4 + (size_t)2 * q * 8 + 3 * swgb::kSlots * 8 + (size_t)2 * q * 4 : 0;
   return spins + 4 * words + 4 * N + hook_words * 4 + ntiles * 4 + swgb::handle_block_bytes() + clock;
 }
 

@@ -77,10 +77,14 @@ uint32_t bond_threshold(int model, double T) {
 // x_a x_b <= 0.
 constexpr double kPi = 3.141592653589793238463;
 
-void clock_tables(int q, double T, std::vector<uint32_t>& tab, std::vector<long long>& fix) {
+void clock_tables(int q, double T, std::vector<uint32_t>& tab, std::vector<long long>& fix,
+                  std::vector<float>& proj) {
   const int q2 = 2 * q;
   std::vector<double> x(q2);
   for (int k = 0; k < q2; ++k) x[k] = std::sin((kPi * (double)k) / (double)q);
+  // the projections in float: the bond kernel's estimate of a threshold
+  proj.assign(q2, 0.0f);
+  for (int k = 0; k < q2; ++k) proj[k] = (float)x[k];
   const double twoK = 2.0 / T;
   tab.assign((size_t)q2 * q2, 0u);
   for (int a = 0; a < q2; ++a)
@@ -321,10 +325,11 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
     // clock tables (thresholds, fixed-point cos/sin) and slot sums in one allocation
     std::vector<uint32_t> tab;
     std::vector<long long> trig;
-    clock_tables(q, T, tab, trig);
+    std::vector<float> proj;
+    clock_tables(q, T, tab, trig, proj);
     const size_t tab_bytes = tab.size() * 4, trig_bytes = trig.size() * 8;
-    const size_t hist_bytes = (size_t)3 * swgb::kSlots * 8;
-    if ((e = cudaMalloc(&h->d_clock, tab_bytes + trig_bytes + hist_bytes)) != cudaSuccess) {
+    const size_t hist_bytes = (size_t)3 * swgb::kSlots * 8, proj_bytes = proj.size() * 4;
+    if ((e = cudaMalloc(&h->d_clock, tab_bytes + trig_bytes + hist_bytes + proj_bytes)) != cudaSuccess) {
       fail(SW_ERR_OOM, std::string("clock tables: ") + cudaGetErrorString(e));
       cudaGetLastError();
       release(h);
@@ -334,9 +339,12 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
     lat.ctab = reinterpret_cast<const uint32_t*>(c);
     h->meas.cfix = reinterpret_cast<const long long*>(c + tab_bytes);
     h->meas.csums = reinterpret_cast<unsigned long long*>(c + tab_bytes + trig_bytes);
+    lat.cproj = reinterpret_cast<const float*>(c + tab_bytes + trig_bytes + hist_bytes);
     if ((e = cudaMemcpy(c, tab.data(), tab_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c + tab_bytes, trig.data(), trig_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(c + tab_bytes + trig_bytes, 0, hist_bytes)) != cudaSuccess) {
+        (e = cudaMemset(c + tab_bytes + trig_bytes, 0, hist_bytes)) != cudaSuccess ||
+        (e = cudaMemcpy(c + tab_bytes + trig_bytes + hist_bytes, proj.data(), proj_bytes,
+                        cudaMemcpyHostToDevice)) != cudaSuccess) {
       cuda_fail(e, "clock tables");
       release(h);
       return nullptr;

@@ -33,6 +33,7 @@ struct Lattice {
   int model;            // Model
   int dq;               // modulus of the cluster draw: q (Potts) or 2
   const uint32_t* ctab; // clock: bond thresholds [2q][2q]
+  const float* cproj;   // clock: projections x_k = sin(pi k / q) rounded to float [2q]
   uint32_t* hooked;     // per tile: roots hooked by the merge [ntiles * hook_cap]
   uint32_t* nhooked;    // per tile: number of hooked roots [ntiles]
   int hook_cap;         // capacity of a tile's hooked list

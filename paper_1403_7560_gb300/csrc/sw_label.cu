@@ -552,6 +552,10 @@ __global__ void __launch_bounds__(256) k_bonds_xy(const __grid_constant__ Lattic
 // q-state clock: x_i = sin(pi k_i / q), k_i = (2 p_i - s) mod 2q for the
 // sweep's mirror index s; bond (i,d) active iff u(i,d) < t[k_i][k_j] (the
 // table is 0 where x_i x_j <= 0); u(i,d) = word d of Philox(i, sweep, BOND, 0).
+// The comparison is decided from a float estimate of t (the projections in
+// shared memory, __expf) unless the draw lies within a margin far above the
+// estimate's error, where the exact table entry decides: the result is the
+// table's, without a table gather per bond.
 // With MEASURE the same loads measure the incoming state: integer sums of
 // the fixed-point tables C[p_i], S[p_i] and C[(p_i - p_j) mod q], added to
 // the clock slots per block.
@@ -560,11 +564,18 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
                                                       const __grid_constant__ Measure mb) {
   __shared__ uint32_t s_mirror;
   __shared__ long long s_red[256 / 32];
+  __shared__ float s_x[2 * kMaxClockQ];
   if (threadIdx.x == 0) s_mirror = clock_mirror(lat, sweep);
   pdl_wait();
-  __syncthreads();
   const int L = lat.L, lane = threadIdx.x & 31;
   const int q = lat.q, q2 = 2 * q;
+  for (int k = threadIdx.x; k < q2; k += 256) s_x[k] = __ldg(&lat.cproj[k]);
+  __syncthreads();
+  // Error of the float threshold estimate below against the exact table
+  // entry t/2^32 (x rounded to float, products and 2K in float, __expf,
+  // the draw rounded to float): below 2K * 2.5e-7 + 4e-7; the margin is
+  // about four times that, and draws inside it read the exact entry.
+  const float margin = __fadd_rn(0x1p-16f, __fmul_rn(lat.twoK, 0x1p-20f));
   const int mirror = (int)s_mirror;
   const uint32_t nwords = lat.R * (uint32_t)lat.W;
   const uint32_t plane = nwords;
@@ -590,11 +601,23 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
         cx += __ldg(&mb.cfix[pi]);
         sy += __ldg(&mb.cfix[q + pi]);
       }
+      const float xi = s_x[ki];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const int pj = clock_state(sp[jn[d]], q);
         const int kj = wrap_mod(2 * pj - mirror, q2);
-        a |= (uint32_t)(word_of(w, d) < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj])) << d;
+        // the table entry is 0 where x_i x_j <= 0 (the sign of a float
+        // product is the exact one; |x| >= sin(pi/q) off k = 0, q)
+        const float prod = __fmul_rn(xi, s_x[kj]);
+        bool act = false;
+        if (prod > 0.0f) {
+          const uint32_t wd = word_of(w, d);
+          const float pf = __fsub_rn(1.0f, __expf(-__fmul_rn(lat.twoK, prod)));
+          const float diff = __fsub_rn(__fmul_rn(__uint2float_rn(wd), 0x1p-32f), pf);
+          act = (fabsf(diff) > margin) ? diff < 0.0f
+                                       : wd < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj]);
+        }
+        a |= (uint32_t)act << d;
         if (MEASURE) eb += __ldg(&mb.cfix[wrap_mod(pi - pj, q)]);
       }
     }

@@ -101,10 +101,12 @@ def test_larger_3d_lattices_bit_exact(sw, model, L, q, T, sweeps):
 
 @pytest.mark.parametrize("dim,L,q,T", [
     (2, 32, 512, 0.9), (2, 48, 8, 1.0), (2, 37, 3, 0.7), (3, 16, 512, 2.2), (3, 20, 6, 2.0),
-    (3, 9, 1024, 2.1)])
+    (3, 9, 1024, 2.1), (2, 40, 16, 0.15), (3, 24, 512, 0.3), (2, 40, 64, 50.0)])
 def test_clock_sweeps_bit_exact(sw, dim, L, q, T):
     """The q-state clock model (the paper's discretised XY): trajectories and
-    float moments are reproducible bit for bit."""
+    float moments are reproducible bit for bit, from far below to far above
+    the transition (2/T from 0.04 to 13: the kernel's float estimate of the
+    bond threshold and its margin scale with 2/T)."""
     run_exact_parity(sw, CLOCK, dim, L, q, T, seed=4000 + L, sweeps=10)
 
 
