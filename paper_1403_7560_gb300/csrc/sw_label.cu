@@ -565,11 +565,16 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
   __shared__ uint32_t s_mirror;
   __shared__ long long s_red[256 / 32];
   __shared__ float s_x[2 * kMaxClockQ];
+  // the fixed-point cos / sin tables of the measurement (gathered per site)
+  __shared__ long long s_fix[MEASURE ? 2 * kMaxClockQ : 1];
   if (threadIdx.x == 0) s_mirror = clock_mirror(lat, sweep);
   pdl_wait();
   const int L = lat.L, lane = threadIdx.x & 31;
   const int q = lat.q, q2 = 2 * q;
-  for (int k = threadIdx.x; k < q2; k += 256) s_x[k] = __ldg(&lat.cproj[k]);
+  for (int k = threadIdx.x; k < q2; k += 256) {
+    s_x[k] = __ldg(&lat.cproj[k]);
+    if (MEASURE) s_fix[k] = __ldg(&mb.cfix[k]);
+  }
   __syncthreads();
   // Error of the float threshold estimate below against the exact table
   // entry t/2^32 (x rounded to float, products and 2K in float, __expf,
@@ -598,8 +603,8 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
       const int pi = clock_state(sp[i], q);
       const int ki = wrap_mod(2 * pi - mirror, q2);
       if (MEASURE) {
-        cx += __ldg(&mb.cfix[pi]);
-        sy += __ldg(&mb.cfix[q + pi]);
+        cx += s_fix[pi];
+        sy += s_fix[q + pi];
       }
       const float xi = s_x[ki];
 #pragma unroll
@@ -618,7 +623,7 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
                                        : wd < __ldg(&lat.ctab[(size_t)ki * (size_t)q2 + (size_t)kj]);
         }
         a |= (uint32_t)act << d;
-        if (MEASURE) eb += __ldg(&mb.cfix[wrap_mod(pi - pj, q)]);
+        if (MEASURE) eb += s_fix[wrap_mod(pi - pj, q)];
       }
     }
 #pragma unroll
