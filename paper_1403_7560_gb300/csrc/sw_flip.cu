@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_
   pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
   if (*bv.step >= m.nsweeps) return;  // the member has had its sweeps this call
-  merge_tile<S>(m.lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
+  const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
+  merge_tile<S>(lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
 }
 
 constexpr int kFlipThreads = 256, kFlipWarps = kFlipThreads / 32;
@@ -186,9 +187,10 @@ __global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const uint32_t step = *bv.step;
   if (step >= m.nsweeps) return;
+  const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
   if (tile == 0u && (step > 0u || m.measure0))
-    finalize_record<kFlipWarps>(m.lat, m.meas, m.sweep0 + step, s_red, s_rd);
-  compress_tile(m.lat, tile);
+    finalize_record<kFlipWarps>(lat, m.meas, m.sweep0 + step, s_red, s_rd);
+  compress_tile(lat, tile);
 }
 
 // Every site takes its cluster's draw from its own word (local roots, now
@@ -274,10 +276,10 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
   __shared__ long long s_red[NW];
   pdl_wait();
   const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
-  const Lattice& lat = m.lat;
   const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const uint32_t step = *bv.step;
   if (step >= m.nsweeps) return;
+  const Lattice lat = m.lat;  // a private copy: the spin stores cannot alias it
   const uint32_t sweep = m.sweep0 + step + 1u;
   const TileCoord tc = tile_coord<S>(lat, tile);
   const int L = lat.L, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
