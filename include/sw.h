@@ -272,7 +272,8 @@ size_t sw_series_capacity(void);
  * Launch configuration.  A batch's tiles are 32 x tile_y (x tile_z) sites,
  * one CTA (a thread per 32-site row word) per tile, in one of
  * SW_BATCH_TILE_SHAPES shapes: 2D 32x256, 32x128, 32x64; 3D 32x16x16,
- * 32x16x8, 32x8x8 (shape 0 is the single-lattice tile).  The label schedule
+ * 32x16x8, 32x8x8 (single lattices use 32x128 in 2D, shape 1, and
+ * 32x16x16 in 3D, shape 0, which a new batch starts with).  The label schedule
  * is 0 (the Ising tiles in one launch with the two-state layout, the Potts
  * tiles in another) or 1 (all tiles in one launch, the Potts layout).  No
  * configuration changes any result: bonds, draws and canonical labels are

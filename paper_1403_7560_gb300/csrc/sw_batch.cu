@@ -226,6 +226,7 @@ sw_batch* sw_batch_create(int dim) {
     return nullptr;
   }
   b->dim = dim;
+  b->shape = swgb::kSingleShape[dim - 2];
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) b->own_stream = true;
   if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(uint32_t));

@@ -137,8 +137,8 @@ __device__ __forceinline__ uint32_t run_start(uint32_t starts, int b) {
 // ---------------------------------------------------------------- tiles
 // A tile is 32 (one bit-plane word) x TY x TZ sites; one CTA of
 // THREADS = TY*TZ threads (a thread per row word) labels it.  Shape S of
-// dimension D is the S-th entry of the shape table; Tile<D> is shape 0,
-// the single-lattice tile.
+// dimension D is the S-th entry of the shape table; Tile<D> is the
+// single-lattice tile.
 template <int D_, int TY_, int TZ_>
 struct TileShape {
   static constexpr int D = D_, TY = TY_, TZ = TZ_, ROWS = TY_ * TZ_, THREADS = TY_ * TZ_;
@@ -146,7 +146,7 @@ struct TileShape {
 template <int D, int S>
 using ShapeOf = TileShape<D, kShapeTY[D - 2][S], kShapeTZ[D - 2][S]>;
 template <int D>
-using Tile = ShapeOf<D, 0>;
+using Tile = ShapeOf<D, kSingleShape[D - 2]>;
 
 struct TileCoord {
   int tx, x0, y0, z0;

@@ -118,14 +118,14 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   if (hooked && threadIdx.x == 0) lat.nhooked[tile] = (uint32_t)s_n;
 }
 
+// Eight 256-thread CTAs per SM, proportionally more of smaller tiles.
+constexpr int merge_blocks(int threads) { return 8 * 256 / threads > 32 ? 32 : 8 * 256 / threads; }
+
 template <int D>
-__global__ void __launch_bounds__(kTileThreads, 8) k_merge(Lattice lat) {
+__global__ void __launch_bounds__(Tile<D>::THREADS, merge_blocks(Tile<D>::THREADS)) k_merge(Lattice lat) {
   __shared__ MergeSmem<Tile<D>> sm;
   merge_tile<Tile<D>>(lat, blockIdx.x, sm);
 }
-
-// Eight 256-thread CTAs per SM, proportionally more of smaller tiles.
-constexpr int merge_blocks(int threads) { return 8 * 256 / threads > 32 ? 32 : 8 * 256 / threads; }
 
 template <class S>
 __global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_batch(BatchView bv) {
@@ -349,6 +349,7 @@ int merge_capacity_dim(int shape) {
 }  // namespace
 
 int merge_list_capacity(int dim, int shape) {
+  if (shape < 0) shape = kSingleShape[dim - 2];
   return dim == 2 ? merge_capacity_dim<2>(shape) : merge_capacity_dim<3>(shape);
 }
 
@@ -366,8 +367,8 @@ void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words)
 
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  if (lat.dim == 2) return launch_pdl(k_merge<2>, g, kTileThreads, st, lat);
-  return launch_pdl(k_merge<3>, g, kTileThreads, st, lat);
+  if (lat.dim == 2) return launch_pdl(k_merge<2>, g, (unsigned)Tile<2>::THREADS, st, lat);
+  return launch_pdl(k_merge<3>, g, (unsigned)Tile<3>::THREADS, st, lat);
 }
 
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,

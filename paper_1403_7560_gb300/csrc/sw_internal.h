@@ -101,14 +101,15 @@ constexpr int kMaxClockQ = 1024;      // largest q of the clock model
 
 // Tile shapes of the labeling and merge kernels: 32 sites along x (one
 // bit-plane word) by TY (by TZ); one CTA of TY*TZ threads (a thread per row
-// word) per tile.  Shape 0 of each dimension is the one single lattices
-// use; a batch runs any of them (sw_batch_autotune times them).  A tile's
-// shape changes no result: bond words, draws and canonical roots are keyed
-// by row word and site index only.
+// word) per tile.  Single lattices use shape kSingleShape of their
+// dimension (2D 32 x 128, 3D 32 x 16 x 16, the faster ones on the GB300);
+// a batch runs any of them (sw_batch_autotune times them).  A tile's shape
+// changes no result: bond words, draws and canonical roots are keyed by row
+// word and site index only.
 constexpr int kTileShapes = 3;
 constexpr int kShapeTY[2][kTileShapes] = {{256, 128, 64}, {16, 16, 8}};
 constexpr int kShapeTZ[2][kTileShapes] = {{1, 1, 1}, {16, 8, 8}};
-constexpr int kTileThreads = 256;  // threads of a shape-0 tile (2D and 3D)
+constexpr int kSingleShape[2] = {1, 0};
 
 // Launches kernel k with programmatic stream serialisation: its launch is
 // processed while the preceding kernel in the stream runs, and it waits for
@@ -130,14 +131,15 @@ cudaError_t launch_pdl(void (*k)(K...), unsigned grid, unsigned block, cudaStrea
   return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
 }
 
-// Tiles per axis of an L^dim lattice in tile shape `shape` (default 0).
-void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz, int shape = 0);
+// Tiles per axis of an L^dim lattice in tile shape `shape` (-1: the
+// single-lattice shape of dim).
+void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz, int shape = -1);
 // Bonds that leave one tile (its +x, +y, +z faces): the most roots one
 // tile's merge can hook.
-int merge_list_capacity(int dim, int shape = 0);
+int merge_list_capacity(int dim, int shape = -1);
 // Sizes of a lattice's per-tile buffers (the hooked-root counters and
 // lists): for Ising/Potts lattices, which may join a batch, the largest
-// over all tile shapes; for the others, shape 0's.
+// over all tile shapes; for the others, the single-lattice shape's.
 void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words);
 
 // Message returned by sw_last_error() on the calling thread.

@@ -313,10 +313,10 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   }
 }
 
+// Five 256-thread CTAs per SM, proportionally more of smaller tiles.
 template <int D, bool FROM_MASK, int MM>
-__global__ void __launch_bounds__(kTileThreads, 5) k_label(const __grid_constant__ Lattice lat, uint32_t sweep,
-                                                              const __grid_constant__ Measure mb) {
-  static_assert(Tile<D>::THREADS == kTileThreads, "shape-0 tiles");
+__global__ void __launch_bounds__(Tile<D>::THREADS, 5 * 256 / Tile<D>::THREADS)
+    k_label(const __grid_constant__ Lattice lat, uint32_t sweep, const __grid_constant__ Measure mb) {
   __shared__ LabelSmem<Tile<D>, MM> sm;
   label_tile<Tile<D>, FROM_MASK, MM>(lat, blockIdx.x, sweep, mb, sm);
 }
@@ -654,6 +654,7 @@ cudaError_t launch_bonds_clock(const Lattice& lat, uint32_t sweep, const Measure
 }
 
 void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz, int shape) {
+  if (shape < 0) shape = kSingleShape[dim - 2];
   const int ty = kShapeTY[dim - 2][shape], tz = kShapeTZ[dim - 2][shape];
   *ntx = (L + 31) / 32;
   *nty = (L + ty - 1) / ty;
@@ -665,11 +666,11 @@ cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cud
   cudaError_t e = cudaSuccess;
   const Measure none{};
   if (lat.dim == 2) {
-    if (from_mask) e = launch_pdl(k_label<2, true, 0>, g, kTileThreads, st, lat, sweep, none);
-    else e = launch_pdl(k_label<2, false, 0>, g, kTileThreads, st, lat, sweep, none);
+    if (from_mask) e = launch_pdl(k_label<2, true, 0>, g, (unsigned)Tile<2>::THREADS, st, lat, sweep, none);
+    else e = launch_pdl(k_label<2, false, 0>, g, (unsigned)Tile<2>::THREADS, st, lat, sweep, none);
   } else {
-    if (from_mask) e = launch_pdl(k_label<3, true, 0>, g, kTileThreads, st, lat, sweep, none);
-    else e = launch_pdl(k_label<3, false, 0>, g, kTileThreads, st, lat, sweep, none);
+    if (from_mask) e = launch_pdl(k_label<3, true, 0>, g, (unsigned)Tile<3>::THREADS, st, lat, sweep, none);
+    else e = launch_pdl(k_label<3, false, 0>, g, (unsigned)Tile<3>::THREADS, st, lat, sweep, none);
   }
   return e;
 }
@@ -728,11 +729,11 @@ cudaError_t launch_label_measured(const Lattice& lat, uint32_t sweep, const Meas
   cudaError_t e = cudaSuccess;
   const bool potts = lat.model == kPotts;
   if (lat.dim == 2) {
-    if (potts) e = launch_pdl(k_label<2, false, 2>, g, kTileThreads, st, lat, sweep, m);
-    else e = launch_pdl(k_label<2, false, 1>, g, kTileThreads, st, lat, sweep, m);
+    if (potts) e = launch_pdl(k_label<2, false, 2>, g, (unsigned)Tile<2>::THREADS, st, lat, sweep, m);
+    else e = launch_pdl(k_label<2, false, 1>, g, (unsigned)Tile<2>::THREADS, st, lat, sweep, m);
   } else {
-    if (potts) e = launch_pdl(k_label<3, false, 2>, g, kTileThreads, st, lat, sweep, m);
-    else e = launch_pdl(k_label<3, false, 1>, g, kTileThreads, st, lat, sweep, m);
+    if (potts) e = launch_pdl(k_label<3, false, 2>, g, (unsigned)Tile<3>::THREADS, st, lat, sweep, m);
+    else e = launch_pdl(k_label<3, false, 1>, g, (unsigned)Tile<3>::THREADS, st, lat, sweep, m);
   }
   return e;
 }
