@@ -274,10 +274,10 @@ size_t small_layout_bytes_max() {
 
 uint32_t small_sites_limit(int model, int dim) {
   // measured on the GB300 against the tiled path (with its overlapped
-  // launches), µs per measured sweep at T_c: 2D Ising L = 64: 25.3 both,
-  // L = 80: 31.2 here, 27.7 tiled; 2D Potts q = 4 L = 90: 32.3 here, 37.5
-  // tiled; 3D Ising L = 8: 17.4 here, 18.7 tiled, L = 12: 25.9 here, 24.4
-  // tiled; 3D Potts q = 3 L = 16: 37.9 here, 34.9 tiled
+  // launches), µs per measured sweep at T_c: 2D Ising L = 64: 25.3 here,
+  // 27.1 tiled, L = 80: 31.1 here, 29.7 tiled; 2D Potts q = 4 L = 90: 32.3
+  // here, 38.2 tiled; 3D Ising L = 8: 17.4 here, 18.7 tiled, L = 12: 25.9
+  // here, 24.4 tiled; 3D Potts q = 3 L = 16: 37.9 here, 34.9 tiled
   if (dim == 2) return model == kPotts ? (uint32_t)kSmallSites : 4096u;
   return 1024u;
 }
