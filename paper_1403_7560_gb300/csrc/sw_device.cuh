@@ -201,20 +201,9 @@ __device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b, in
 // draw, shift = sb + 1, marker = 1 << sb set on every local root (the only
 // nodes these functions touch).  Links always point to a smaller index, so
 // the root of every tree is its smallest site index.
-__device__ __forceinline__ uint32_t gfind(uint32_t* f, uint32_t x, int shift, uint32_t marker) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    const uint32_t p = __ldcg(&f[x]) >> shift;
-    if (p == x) return x;
-    const uint32_t gp = __ldcg(&f[p]) >> shift;
-    if (gp == p) return p;
-    __stcg(&f[x], (gp << shift) | marker);  // path halving on a non-root
-    x = gp;
-  }
-  return x;
-}
-
 // The roots of a and b, the two walks advanced in lockstep so that their
-// loads are in flight together (path halving as in gfind).
+// loads are in flight together; each step on a non-root halves its path
+// (the word of the node walked from is pointed at its grandparent).
 __device__ __forceinline__ void gfind2(uint32_t* f, uint32_t& a, uint32_t& b, int shift, uint32_t marker) {
   bool da = false, db = false;
   for (int it = 0; it < (1 << 22); ++it) {
