@@ -59,3 +59,34 @@ def test_clock_parser_keeps_only_the_timed_window():
     assert c["samples"] == 2 and c["sm_mhz"] == pytest.approx(2017.5)
     assert c["reasons"] == ["sw_power_cap"]
     assert bench.Clocks.parse("", t0, t0 + 1)["samples"] == 0
+
+
+def test_batch_launch_count():
+    """The gpu_launches claim of the batch lines: labels (one per model under
+    schedule 0, one under schedule 1), merge, compression, apply, one small
+    kernel per model with one-CTA members, the step counter."""
+    import bench
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import inputs
+    ising, potts = inputs.ISING, inputs.POTTS
+    big = [(ising, 2, 1024, 2, 2.0, 1), (potts, 2, 512, 3, 1.0, 2)]
+    small = [(ising, 2, 32, 2, 2.0, 3), (potts, 2, 90, 4, 0.9, 4), (ising, 2, 80, 2, 2.0, 5)]
+    assert bench.batch_launches(big, 0) == 2 + 3 + 1
+    assert bench.batch_launches(big, 1) == 1 + 3 + 1
+    # Ising L = 80 (6400 sites) is tiled, Potts L = 90 (8100) and Ising L = 32 are one-CTA
+    assert bench.batch_launches(small, 0) == 1 + 3 + 2 + 1
+    assert bench.batch_launches([(ising, 3, 10, 2, 4.5, 6)], 0) == 0 + 0 + 1 + 1
+    assert bench.batch_launches([(ising, 3, 11, 2, 4.5, 6)], 0) == 1 + 3 + 0 + 1
+
+
+def test_workload_recipes():
+    """The seeded batch recipes stay within their stated ranges."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import inputs
+    for specs, lo, hi in ((inputs.ragged_batch(256, 1003), 32, 1024), (inputs.small_batch(256, 1005), 16, 90)):
+        assert len(specs) == 256
+        for model, dim, L, q, T, seed in specs:
+            assert dim == 2 and lo <= L <= hi and q in (2, 3, 4) and seed > 0
+            tc = inputs.TC_2D_ISING if model == inputs.ISING else inputs.tc_2d_potts(q)
+            assert 0.8 * tc <= T <= 1.2 * tc
+    assert inputs.small_batch(8, 7) == inputs.small_batch(8, 7)
