@@ -49,3 +49,18 @@ def test_clock_threshold_estimate_within_its_margin(q, T):
     assert np.all(t[~pos] == 0.0)
     # the draw's float conversion adds at most 2^-25 (u < 1): inside the margin's slack
     assert margin - bound > 2.0 ** -25
+
+
+@pytest.mark.parametrize("T", [0.05, 0.89, 2.20184, 50.0])
+def test_xy_exp_estimate_within_its_margin(T):
+    """XY bonds: from the (accurate) projection product, the kernel takes
+    p from 1 - __expf(-2K prod) and calls expm1f only when the draw lies
+    within 2^-16 of it; the estimate must stay far inside that margin for
+    every product in (0, 1]."""
+    prod = np.linspace(1e-7, 1.0, 2_000_001, dtype=np.float64).astype(np.float32)
+    twoK = np.float32(2.0 / T)
+    a = (twoK * prod).astype(np.float32)
+    e = np.exp(-a).astype(np.float32)
+    pf = (np.float32(1.0) - e).astype(np.float64) + 2.0 * np.spacing(e).astype(np.float64)
+    exact = -np.expm1(-a.astype(np.float64))
+    assert np.abs(pf - exact).max() < 2.0 ** -16 / 8
