@@ -3,6 +3,9 @@ same float32 operations (numpy rounds each float32 operation to nearest;
 the one transcendental, the GPU's __expf, is given its documented extra
 error of 2 ulp).
 
+XY bonds: the exp estimate stays far inside the 2^-16 margin of its
+expm1f fallback (test_xy_exp_estimate_within_its_margin).
+
 Clock model bonds: the kernel decides u < t[k_a][k_b] from the float
 estimate pf = 1 - exp(-(2/T) x_a x_b) with x_k = float(sin(pi k / q)) and
 reads the exact table entry only when |u - pf| <= 2^-16 + (2/T) 2^-20.  Its
