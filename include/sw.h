@@ -328,8 +328,10 @@ int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep);
  *     sweeps enqueued afterwards start from it.  The measurement pending on
  *     the replaced state is taken first, as in sw_set_spins.
  * sw_get_spins_async(h, host, bytes)  enqueues the download of the state
- *     after the sweeps enqueued so far (a device-side snapshot is taken on
- *     the handle's stream, so later sweeps do not wait for the transfer).
+ *     after the sweeps enqueued so far: a device-side snapshot, then the
+ *     host copy, both on the download stream; later sweeps run meanwhile
+ *     and only the next write of the snapshotted buffer waits for the
+ *     snapshot (not for the host copy).
  * sw_get_record_async(h, sweep, host) enqueues the download of the record of
  *     a measured sweep (1 <= sweep <= sw_sweep_counter and among the last
  *     sw_series_capacity sweeps, else SW_ERR_RANGE) into one sw_record; the
