@@ -86,3 +86,21 @@ def test_product_path_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text
                 assert "sw_oracle" not in text and "liboracle" not in text
+
+
+def test_device_bytes_accounting(swlib):
+    """sw_device_bytes (host arithmetic, no GPU): the spins, bond planes and
+    forest at least; tile buffers sized for every batch tile shape for
+    Ising/Potts; the clock tables; 0 for invalid arguments."""
+    db = swlib.sw_device_bytes
+    N = 256 ** 3
+    ising = db(swlib.SW_ISING, 3, 256, 2)
+    assert ising >= N + 3 * N // 8 + 4 * N
+    # the 32x8x8 tiles of a batch: 8192 tiles of 576 hooked words, counted for a batchable lattice
+    assert ising >= N + 3 * N // 8 + 4 * N + 8192 * 576 * 4
+    assert db(swlib.SW_XY, 3, 256, 2) >= 4 * N + 3 * N // 8 + 4 * N
+    q = 512
+    assert db(swlib.SW_CLOCK, 3, 64, q) - db(swlib.SW_CLOCK, 3, 64, 3) >= 4 * (2 * q) ** 2 - 4 * 36
+    assert db(swlib.SW_ISING, 2, 64, 2) < db(swlib.SW_ISING, 2, 128, 2) < db(swlib.SW_ISING, 2, 256, 2)
+    for bad in ((9, 2, 16, 2), (0, 4, 16, 2), (0, 2, 3, 2), (0, 3, 2000, 2)):
+        assert db(*bad) == 0
