@@ -164,3 +164,58 @@ def enumerate_clock(dim: int, L: int, q: int, T: float) -> dict:
     w = np.exp(-(E - E.min()) / T)
     Z = w.sum()
     return {"E": (w * E).sum() / Z, "M2": (w * M2).sum() / Z, "M4": (w * M2 ** 2).sum() / Z}
+
+
+_DOS_CACHE: dict = {}
+
+
+def ising_density_of_states(dim: int, L: int, chunk_bits: int = 22) -> np.ndarray:
+    """g[u, n]: the number of Ising configurations of the periodic L^dim
+    lattice with u unsatisfied (antiparallel) bonds and n up spins, by
+    enumeration of all 2^N states as N-bit integers (N <= 32).  The +d
+    neighbour of every site is a fixed bit permutation, applied to a whole
+    chunk of states with shifts and masks; u is the popcount of the state
+    xor its permuted copy.  Cached per lattice."""
+    key = (dim, L)
+    if key in _DOS_CACHE:
+        return _DOS_CACHE[key]
+    N = L ** dim
+    assert N <= 32
+    groups = []
+    for d in range(dim):
+        nb = neighbours(dim, L, d)
+        by_shift: dict = {}
+        for i in range(N):
+            by_shift[int(nb[i]) - i] = by_shift.get(int(nb[i]) - i, 0) | (1 << i)
+        groups.append([(delta, np.uint32(mask)) for delta, mask in by_shift.items()])
+    nbonds = dim * N
+    hist = np.zeros((nbonds + 1) * (N + 1), dtype=np.int64)
+    step = 1 << min(chunk_bits, N)
+    for start in range(0, 1 << N, step):
+        S = np.arange(start, start + step, dtype=np.uint64).astype(np.uint32)
+        u = np.zeros(step, dtype=np.int64)
+        for d in range(dim):
+            R = np.zeros(step, dtype=np.uint32)
+            for delta, mask in groups[d]:
+                # bit i of R is bit nb(i) = i + delta of S
+                R |= ((S >> np.uint32(delta)) if delta > 0 else (S << np.uint32(-delta))) & mask
+            u += np.bitwise_count(S ^ R).astype(np.int64)
+        n_up = np.bitwise_count(S).astype(np.int64)
+        hist += np.bincount(u * (N + 1) + n_up, minlength=hist.size)
+    g = hist.reshape(nbonds + 1, N + 1)
+    _DOS_CACHE[key] = g
+    return g
+
+
+def ising_moments_from_dos(dim: int, L: int, T: float) -> dict:
+    """Exact <E>, <E^2>, <M^2>, <M^4> of the Ising model (E = -sum s_i s_j,
+    M = sum s_i) from the enumerated density of states."""
+    g = ising_density_of_states(dim, L).astype(np.float64)
+    N = L ** dim
+    nbonds = dim * N
+    E = -(nbonds - 2.0 * np.arange(nbonds + 1))[:, None]
+    M = (2.0 * np.arange(N + 1) - N)[None, :]
+    w = g * np.exp(-(E - E.min()) / T)
+    Z = w.sum()
+    return {"E": (w * E).sum() / Z, "E2": (w * E * E).sum() / Z,
+            "M2": (w * M ** 2).sum() / Z, "M4": (w * M ** 4).sum() / Z}

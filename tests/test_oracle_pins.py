@@ -282,6 +282,110 @@ def test_ising_energy_vs_kaufman(L):
     assert abs(mean[0] - ex) < 4.5 * err[0], (mean[0], ex, err[0])
 
 
+def test_density_of_states_matches_brute_enumeration():
+    # the bit-permutation enumeration against the configuration-array one
+    for dim, L in [(2, 4), (2, 3), (3, 2)]:
+        for T in (1.5, 3.0):
+            a, b = exact.ising_moments_from_dos(dim, L, T), exact.enumerate_ising(dim, L, T)
+            for k in ("E", "E2", "M2", "M4"):
+                assert a[k] == pytest.approx(b[k], rel=1e-12), (dim, L, T, k)
+
+
+@pytest.mark.parametrize("T", [3.0, 4.5115])
+def test_ising_3x3x3_enumeration(T):
+    """3D Ising on the 3x3x3 torus, the smallest 3D lattice whose +d and -d
+    bonds of a site are different pairs (all 2^27 states enumerated)."""
+    ex = exact.ising_moments_from_dos(3, 3, T)
+    o = oracle.Oracle(ISING, 3, 3, 2, T, seed=333)
+    o.sweep(500, measure=False)
+    mean, err = _binned(o, 24, 6000)
+    o.close()
+    _check(mean, err, ex, ["E", "M2", "M4", "E2"])
+
+
+def test_binder_ratio_4x4_enumeration():
+    """U = <M^4>/<M^2>^2 (Sec. 3) from the oracle's accumulators against the
+    exact ratio of the 4x4 Ising torus at T_c (jackknife error over bins)."""
+    T = 2.0 / math.log(1.0 + math.sqrt(2.0))
+    ex = exact.enumerate_ising(2, 4, T)
+    o = oracle.Oracle(ISING, 2, 4, 2, T, seed=404)
+    o.sweep(500, measure=False)
+    o.take_acc()
+    m2, m4 = [], []
+    for _ in range(24):
+        o.sweep(6000)
+        a = o.take_acc()
+        m2.append(a["sum_M2"] / a["n_sweeps"])
+        m4.append(a["sum_M4"] / a["n_sweeps"])
+    o.close()
+    U, err = _jackknife_ratio(np.array(m4), np.array(m2))
+    assert abs(U - ex["M4"] / ex["M2"] ** 2) < 4.5 * err, (U, ex["M4"] / ex["M2"] ** 2, err)
+
+
+def _jackknife_ratio(m4, m2):
+    """U = mean(m4)/mean(m2)^2 and its jackknife standard error over bins."""
+    n = m4.size
+    jk = ((m4.sum() - m4) / (n - 1)) / ((m2.sum() - m2) / (n - 1)) ** 2
+    return m4.mean() / m2.mean() ** 2, math.sqrt((n - 1) / n * ((jk - jk.mean()) ** 2).sum())
+
+
+def test_kaufman_energy_at_the_critical_point_tends_to_minus_sqrt2():
+    """At T_c = 2/ln(1 + sqrt 2) the infinite-lattice energy per site of the
+    square-lattice Ising model is -sqrt 2 (Onsager); Kaufman's finite tori
+    approach it as 1/L.  A fit e(L) = e_inf + a/L + b/L^2 over L = 64, 128,
+    256 gives e_inf to 1e-6."""
+    Tc = 2.0 / math.log(1.0 + math.sqrt(2.0))
+    Ls = np.array([64.0, 128.0, 256.0])
+    e = np.array([exact.kaufman_energy(int(L), Tc) / L ** 2 for L in Ls])
+    A = np.stack([np.ones(3), 1.0 / Ls, 1.0 / Ls ** 2], axis=1)
+    e_inf = np.linalg.solve(A, e)[0]
+    assert abs(e_inf + math.sqrt(2.0)) < 1e-6, e_inf
+    assert np.all(np.diff(np.abs(e + math.sqrt(2.0))) < 0)
+
+
+def test_oracle_energy_at_the_2d_ising_critical_point():
+    """The oracle at T_c = 2/ln(1 + sqrt 2) on the 32 x 32 torus: <E>
+    within 3 standard errors of Kaufman's exact value."""
+    L, Tc = 32, 2.0 / math.log(1.0 + math.sqrt(2.0))
+    o = oracle.Oracle(ISING, 2, L, 2, Tc, seed=2269)
+    o.sweep(300, measure=False)
+    mean, err = _binned(o, 20, 600)
+    o.close()
+    ex = exact.kaufman_energy(L, Tc)
+    assert abs(mean[0] - ex) < 3.0 * err[0], (mean[0], ex, err[0])
+
+
+def _binder(model, L, q, T, seed, bins=12, per=1500):
+    o = oracle.Oracle(model, 2, L, q, T, seed)
+    o.sweep(1000, measure=False)
+    o.take_acc()
+    m2, m4 = [], []
+    for _ in range(bins):
+        o.sweep(per)
+        a = o.take_acc()
+        m2.append(a["sum_M2"] / a["n_sweeps"])
+        m4.append(a["sum_M4"] / a["n_sweeps"])
+    o.close()
+    return _jackknife_ratio(np.array(m4), np.array(m2))
+
+
+@pytest.mark.parametrize("model,q,Tc", [
+    (ISING, 2, 2.0 / math.log(1.0 + math.sqrt(2.0))),
+    (POTTS, 3, 1.0 / math.log(1.0 + math.sqrt(3.0))),
+    (POTTS, 4, 1.0 / math.log(1.0 + math.sqrt(4.0)))])
+def test_binder_crossing_brackets_the_critical_point(model, q, Tc):
+    """The ratio U of L = 16 and L = 32 cross at the 2D critical point:
+    below it U falls with L (order), above it U rises (disorder).  The sign
+    of U(32) - U(16) at 0.97 T_c and at 1.03 T_c, each at least 5 standard
+    errors, brackets the crossing within 3% of T_c = 2/ln(1 + sqrt 2)
+    (Ising) and 1/ln(1 + sqrt q) (Potts, duality).  A wrong factor in the
+    bond probability (2K for Potts) or in T would move it by tens of %."""
+    for f, sign in [(0.97, -1.0), (1.03, 1.0)]:
+        u16, e16 = _binder(model, 16, q, f * Tc, seed=600 + q)
+        u32, e32 = _binder(model, 32, q, f * Tc, seed=700 + q)
+        assert sign * (u32 - u16) > 5.0 * math.hypot(e16, e32), (f, u16, e16, u32, e32)
+
+
 def test_potts_q2_is_ising_at_half_temperature():
     # H_Potts(q=2) = (H_Ising + const)/2 per bond: Potts at T/2 has the Ising
     # bond probability 1 - exp(-2/T).  Init and draw maps: Ising +1 <-> 0.
