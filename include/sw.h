@@ -155,6 +155,27 @@ int sw_measure(sw_handle* h, sw_moments* out);
 /* Synchronise the handle's stream and report any device error flag. */
 int sw_sync(sw_handle* h);
 
+/* Failure-detection hook (no counterpart in the paper).  Every device loop
+ * whose trip count depends on the data -- the union retries of the tile
+ * labeling (shared memory) and of the global merge, the compression and
+ * canonical-label walks, the label-equivalence walks and iterations of
+ * sw_relabel -- is capped.  On valid input each ends far below the cap
+ * (parents only decrease), so the cap only turns a corrupted forest into an
+ * error instead of a hang: a loop that reaches it writes SW_ERR_TIMEOUT to
+ * the handle's device error flag and gives up, the kernel returns, and the
+ * next synchronising call (sw_sync, sw_measure, the getters,
+ * sw_label_from_bonds, sw_relabel) returns SW_ERR_TIMEOUT and clears the
+ * flag.  The results of the affected call are then undefined; the handle
+ * itself stays usable.
+ *   cap >= 0   every capped loop of this handle's own launches gives up
+ *              after cap steps (0: at once; used by the tests to exercise
+ *              the error path without a fault)
+ *   cap < 0    restores the production cap (2^22 steps)
+ * Takes effect for launches enqueued after the call; a batch member keeps
+ * the cap it had when it joined its batch.  Returns SW_ERR_BAD_ARG for a
+ * NULL handle or cap > 2^22. */
+int sw_set_loop_cap(sw_handle* h, long long cap);
+
 /* Use `stream` (a cudaStream_t, e.g. torch.cuda.Stream.cuda_stream; NULL =
  * the legacy default stream) for all further work of the handle.  The
  * caller keeps ownership of the stream and must keep it alive while the
@@ -366,9 +387,11 @@ int sw_wait_io(sw_handle* h);
  *   dev_labels   device pointer, L^dim int32 labels (written)
  *   stream       cudaStream_t to run on (NULL = legacy default stream)
  *
- * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call on a device shares the same array and leaves
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress), so the call stays valid across cudaDeviceReset.
+ * The call cannot be captured into a CUDA graph: it reads its error flag
+ * back and synchronises `stream`, so on a capturing stream it returns
+ * SW_ERR_BAD_ARG before any GPU work.  Every call on a device shares the same array and leaves
  * its contents behind; the call clears the error flag itself, and the forest
  * needs no clearing.  Calls whose GPU work overlaps (on different streams or
  * from different threads) race on the array and must be serialised by the

@@ -109,33 +109,36 @@ int rebuild(sw_batch* b) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch sync");
   if (b->members.size() > b->cap_members) {
-    cudaFree(b->d_members);
+    swgb::dev_free(b->d_members, b->stream);
     cudaFreeHost(b->h_members);
     b->d_members = nullptr;
     b->h_members = nullptr;
     const size_t cap = std::max<size_t>(16, b->members.size() * 2);
-    if ((e = cudaMalloc(&b->d_members, cap * sizeof(BatchMember))) != cudaSuccess ||
+    if ((e = swgb::dev_alloc((void**)&b->d_members, cap * sizeof(BatchMember), b->stream)) != cudaSuccess ||
         (e = cudaMallocHost(&b->h_members, cap * sizeof(BatchMember))) != cudaSuccess)
       return bfail(SW_ERR_OOM, std::string("batch descriptors: ") + cudaGetErrorString(e));
     b->cap_members = cap;
   }
   if (ntiles > b->cap_tiles) {
-    cudaFree(b->d_tiles);
+    swgb::dev_free(b->d_tiles, b->stream);
     b->d_tiles = nullptr;
     const size_t cap = std::max<size_t>(1024, ntiles * 2);
-    if ((e = cudaMalloc(&b->d_tiles, 2 * cap * sizeof(uint32_t))) != cudaSuccess)
+    if ((e = swgb::dev_alloc((void**)&b->d_tiles, 2 * cap * sizeof(uint32_t), b->stream)) != cudaSuccess)
       return bfail(SW_ERR_OOM, std::string("batch tile map: ") + cudaGetErrorString(e));
     b->cap_tiles = cap;
   }
   const size_t nsmall = small_ising.size() + small_potts.size();
   if (nsmall > b->cap_small) {
-    cudaFree(b->d_small);
+    swgb::dev_free(b->d_small, b->stream);
     b->d_small = nullptr;
     const size_t cap = std::max<size_t>(64, nsmall * 2);
-    if ((e = cudaMalloc(&b->d_small, cap * sizeof(uint32_t))) != cudaSuccess)
+    if ((e = swgb::dev_alloc((void**)&b->d_small, cap * sizeof(uint32_t), b->stream)) != cudaSuccess)
       return bfail(SW_ERR_OOM, std::string("batch small-member list: ") + cudaGetErrorString(e));
     b->cap_small = cap;
   }
+  // the (re)allocations above are ordered on the batch stream; the copies
+  // below run on the legacy stream
+  if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(e, "batch sync");
   if (nsmall) {
     std::vector<uint32_t> all(small_ising);
     all.insert(all.end(), small_potts.begin(), small_potts.end());
@@ -229,7 +232,8 @@ sw_batch* sw_batch_create(int dim) {
   b->shape = swgb::kSingleShape[dim - 2];
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) b->own_stream = true;
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(uint32_t));
+  if (e == cudaSuccess) e = swgb::dev_alloc((void**)&b->d_step, sizeof(uint32_t), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     bcuda(e, "batch create");
@@ -244,11 +248,11 @@ void sw_batch_destroy(sw_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (sw_handle* h : b->members) h->batch = nullptr;
   drop_graph(b);
-  cudaFree(b->d_members);
+  swgb::dev_free(b->d_members, b->stream);
   cudaFreeHost(b->h_members);
-  cudaFree(b->d_tiles);
-  cudaFree(b->d_small);
-  cudaFree(b->d_step);
+  swgb::dev_free(b->d_tiles, b->stream);
+  swgb::dev_free(b->d_small, b->stream);
+  swgb::dev_free(b->d_step, b->stream);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->side) cudaStreamDestroy(b->side);

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -20,6 +21,50 @@ thread_local std::string g_last_error;
 }  // namespace
 
 void swgb::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+constexpr int kMaxPoolDevices = 64;
+// freed memory the pool keeps for reuse before returning any to the driver
+constexpr uint64_t kPoolKeepBytes = 16ull << 30;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t device_pool(cudaMemPool_t* out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+    uint64_t keep = kPoolKeepBytes;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t swgb::dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  const cudaError_t e = device_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void swgb::dev_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
 
 namespace {
 
@@ -114,15 +159,19 @@ int draw_bits(int model, int q) {
 void release(sw_handle* h) {
   if (!h) return;
   swgb::release_io(h);
-  cudaFree(h->lat.spins);
-  cudaFree(h->lat.planes);
-  cudaFree(h->lat.forest);
-  cudaFree(h->lat.hooked);
-  cudaFree(h->lat.nhooked);
-  cudaFree(h->d_labels);
-  cudaFree(h->d_block);
-  cudaFree(h->d_clock);
-  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  // every stream that used the buffers has been synchronised (sw_destroy,
+  // release_io): the frees are ordered on the handle's stream and do not
+  // wait for the rest of the device
+  cudaStream_t st = h->stream;
+  swgb::dev_free(h->lat.spins, st);
+  swgb::dev_free(h->lat.planes, st);
+  swgb::dev_free(h->lat.forest, st);
+  swgb::dev_free(h->lat.hooked, st);
+  swgb::dev_free(h->lat.nhooked, st);
+  swgb::dev_free(h->d_labels, st);
+  swgb::dev_free(h->d_block, st);
+  swgb::dev_free(h->d_clock, st);
+  if (h->own_stream && st) cudaStreamDestroy(st);
   delete h;
 }
 
@@ -284,6 +333,7 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   lat.model = model;
   h->bond_words = (size_t)dim * lat.R * (size_t)lat.W;
   lat.hook_cap = swgb::merge_list_capacity(dim);
+  lat.cap = swgb::kLoopCap;
   size_t tile_bufs = 0, hook_words = 0;  // sized for every tile shape a batch may use
   swgb::tile_buffers(model, dim, L, &tile_bufs, &hook_words);
 
@@ -297,12 +347,13 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
   const size_t off_hist = bl.hist, off_pd = bl.pd, off_series = bl.series;
   const size_t block_bytes = bl.total;
 
-  if ((e = cudaMalloc(&lat.spins, h->spin_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&lat.planes, h->bond_words * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&lat.forest, (size_t)N * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&lat.hooked, hook_words * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&lat.nhooked, tile_bufs * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_block, block_bytes)) != cudaSuccess) {
+  cudaStream_t st = h->stream;
+  if ((e = swgb::dev_alloc(&lat.spins, h->spin_bytes, st)) != cudaSuccess ||
+      (e = swgb::dev_alloc((void**)&lat.planes, h->bond_words * 4, st)) != cudaSuccess ||
+      (e = swgb::dev_alloc((void**)&lat.forest, (size_t)N * 4, st)) != cudaSuccess ||
+      (e = swgb::dev_alloc((void**)&lat.hooked, hook_words * 4, st)) != cudaSuccess ||
+      (e = swgb::dev_alloc((void**)&lat.nhooked, tile_bufs * 4, st)) != cudaSuccess ||
+      (e = swgb::dev_alloc(&h->d_block, block_bytes, st)) != cudaSuccess) {
     fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,
          std::string("device allocation: ") + cudaGetErrorString(e));
     cudaGetLastError();
@@ -329,7 +380,7 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
     clock_tables(q, T, tab, trig, proj);
     const size_t tab_bytes = tab.size() * 4, trig_bytes = trig.size() * 8;
     const size_t hist_bytes = (size_t)3 * swgb::kSlots * 8, proj_bytes = proj.size() * 4;
-    if ((e = cudaMalloc(&h->d_clock, tab_bytes + trig_bytes + hist_bytes + proj_bytes)) != cudaSuccess) {
+    if ((e = swgb::dev_alloc(&h->d_clock, tab_bytes + trig_bytes + hist_bytes + proj_bytes, st)) != cudaSuccess) {
       fail(SW_ERR_OOM, std::string("clock tables: ") + cudaGetErrorString(e));
       cudaGetLastError();
       release(h);
@@ -340,11 +391,14 @@ sw_handle* sw_create(int model, int dim, int L, int q, double T, uint64_t seed) 
     h->meas.cfix = reinterpret_cast<const long long*>(c + tab_bytes);
     h->meas.csums = reinterpret_cast<unsigned long long*>(c + tab_bytes + trig_bytes);
     lat.cproj = reinterpret_cast<const float*>(c + tab_bytes + trig_bytes + hist_bytes);
-    if ((e = cudaMemcpy(c, tab.data(), tab_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(c + tab_bytes, trig.data(), trig_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(c + tab_bytes + trig_bytes, 0, hist_bytes)) != cudaSuccess ||
-        (e = cudaMemcpy(c + tab_bytes + trig_bytes + hist_bytes, proj.data(), proj_bytes,
-                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+    // copies on the allocating stream, from host vectors that live until
+    // the synchronisation at the end of sw_create
+    if ((e = cudaMemcpyAsync(c, tab.data(), tab_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c + tab_bytes, trig.data(), trig_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c + tab_bytes + trig_bytes, 0, hist_bytes, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c + tab_bytes + trig_bytes + hist_bytes, proj.data(), proj_bytes,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
       cuda_fail(e, "clock tables");
       release(h);
       return nullptr;
@@ -401,6 +455,13 @@ int sw_sync(sw_handle* h) {
   const cudaError_t e = swgb::wait_io(h);
   if (e != cudaSuccess) return cuda_fail(e, "asynchronous I/O");
   return check_device_error(h);
+}
+
+int sw_set_loop_cap(sw_handle* h, long long cap) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  if (cap > (long long)swgb::kLoopCap) return fail(SW_ERR_BAD_ARG, "cap above the production cap 2^22");
+  h->lat.cap = cap < 0 ? swgb::kLoopCap : (uint32_t)cap;
+  return SW_OK;
 }
 
 int sw_measure(sw_handle* h, sw_moments* out) {
@@ -500,7 +561,7 @@ int sw_get_labels(sw_handle* h, int32_t* host, size_t n) {
   if (!h || !host) return fail(SW_ERR_BAD_ARG, "NULL argument");
   if (n != h->lat.N) return fail(SW_ERR_BAD_ARG, "n != number of sites");
   cudaError_t e = cudaSuccess;
-  if (!h->d_labels) e = cudaMalloc(&h->d_labels, (size_t)h->lat.N * 4);
+  if (!h->d_labels) e = swgb::dev_alloc((void**)&h->d_labels, (size_t)h->lat.N * 4, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "labels buffer");
   if ((e = swgb::launch_labels_out(h->lat, h->d_labels, h->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(host, h->d_labels, n * 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)

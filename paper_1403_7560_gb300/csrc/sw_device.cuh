@@ -179,9 +179,9 @@ __device__ __forceinline__ uint32_t sfind(volatile uint32_t* par, uint32_t x) {
   return x;
 }
 
-__device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b, int* err) {
+__device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b, int* err, uint32_t cap) {
   volatile uint32_t* vp = par;
-  for (int it = 0; it < 65536; ++it) {
+  for (uint32_t it = 0; it < cap; ++it) {
     a = sfind(vp, a);
     b = sfind(vp, b);
     if (a == b) return;
@@ -239,10 +239,11 @@ __device__ __forceinline__ void gfind2(uint32_t* f, uint32_t& a, uint32_t& b, in
 // Joins the trees of a and b; returns the root that was hooked under the
 // other tree (each root is hooked at most once), or 0xffffffff if the two
 // were already one tree.
-__device__ __forceinline__ uint32_t gunion(uint32_t* f, uint32_t a, uint32_t b, int sb, int* err) {
+__device__ __forceinline__ uint32_t gunion(uint32_t* f, uint32_t a, uint32_t b, int sb, int* err,
+                                           uint32_t cap) {
   const int shift = sb + 1;
   const uint32_t marker = 1u << sb;
-  for (int it = 0; it < (1 << 20); ++it) {
+  for (uint32_t it = 0; it < cap; ++it) {
     gfind2(f, a, b, shift, marker);
     if (a == b) return 0xffffffffu;
     if (a < b) {

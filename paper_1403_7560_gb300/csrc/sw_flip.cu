@@ -111,7 +111,7 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   // (no list on the labeling-only paths)
   uint32_t* hooked = lat.hooked ? lat.hooked + (size_t)tile * (size_t)lat.hook_cap : nullptr;
   for (int e = threadIdx.x; e < n; e += NT) {
-    const uint32_t h = gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err);
+    const uint32_t h = gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err, lat.cap);
     if (hooked && h != 0xffffffffu) hooked[atomicAdd(&s_n, 1)] = h;
   }
   __syncthreads();
@@ -151,14 +151,14 @@ __device__ __forceinline__ void compress_tile(const Lattice& lat, uint32_t t) {
   for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
     const uint32_t a = __ldcg(&list[e]);
     uint32_t cur = a, v = __ldcg(&lat.forest[a]);
-    int it = 0;
-    for (; it < (1 << 22); ++it) {
+    uint32_t it = 0;
+    for (; it < lat.cap; ++it) {
       const uint32_t p = v >> shift;
       if (p == cur) break;
       cur = p;
       v = __ldcg(&lat.forest[cur]);
     }
-    if (it == (1 << 22)) atomicExch(lat.err, kErrTimeout);
+    if (it == lat.cap) atomicExch(lat.err, kErrTimeout);
     __stcg(&lat.forest[a], (cur << shift) | lr_bit | (v & dmask));
   }
 }
@@ -326,13 +326,13 @@ __global__ void __launch_bounds__(256) k_labels_out(Lattice lat, int32_t* out) {
   const int shift = lat.sbits + 1;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < lat.N; i += gridDim.x * blockDim.x) {
     uint32_t r = lat.forest[i] >> shift;
-    int it = 0;
-    for (; it < (1 << 22); ++it) {
+    uint32_t it = 0;
+    for (; it < lat.cap; ++it) {
       const uint32_t r2 = lat.forest[r] >> shift;
       if (r2 == r) break;
       r = r2;
     }
-    if (it == (1 << 22)) atomicExch(lat.err, kErrTimeout);
+    if (it == lat.cap) atomicExch(lat.err, kErrTimeout);
     out[i] = (int32_t)r;
   }
 }

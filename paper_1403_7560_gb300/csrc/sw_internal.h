@@ -37,7 +37,15 @@ struct Lattice {
   uint32_t* hooked;     // per tile: roots hooked by the merge [ntiles * hook_cap]
   uint32_t* nhooked;    // per tile: number of hooked roots [ntiles]
   int hook_cap;         // capacity of a tile's hooked list
+  uint32_t cap;         // iteration cap of the capped device loops (kLoopCap unless lowered
+                        // by sw_set_loop_cap); a loop that reaches it sets *err and gives up
 };
+
+// Production iteration cap of the device loops whose length depends on the
+// data (union retries, global union-find and compression walks, the label
+// equivalence walks).  Every such loop ends far below it on valid input:
+// parents only decrease, so a walk is bounded by the index range.
+constexpr uint32_t kLoopCap = 1u << 22;
 
 // Sets the Philox key (seed low, seed high) and its ten round keys.
 inline void set_philox_key(Lattice& lat, uint64_t seed) {
@@ -144,6 +152,15 @@ void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words)
 
 // Message returned by sw_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
+
+// Stream-ordered device memory from a pool the library keeps per device
+// (cudaMallocFromPoolAsync / cudaFreeAsync).  Creating or destroying a
+// handle or a batch therefore never synchronises the device (cudaFree
+// does), and freed blocks stay cached in the pool for the next handle.  An
+// allocation is ordered on `st`: other streams may use it once `st` has
+// been synchronised past it.  dev_free(nullptr, st) does nothing.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
 
 cudaError_t launch_init(const Lattice& lat, int model, cudaStream_t st);
 // Bonds of the XY model (lane per site) into the bit-planes.

@@ -43,8 +43,10 @@ cudaError_t ensure_io(sw_handle* h) {
   if (h->io_in) return cudaSuccess;
   cudaError_t e = cudaStreamCreateWithFlags(&h->io_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, h->spin_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->snap, h->spin_bytes);
+  if (e == cudaSuccess) e = swgb::dev_alloc(&h->stage_in, h->spin_bytes, h->stream);
+  if (e == cudaSuccess) e = swgb::dev_alloc(&h->snap, h->spin_bytes, h->stream);
+  // the copy streams use the buffers: order them after the allocations
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaEvent_t* evs[6] = {&h->ev_in_done, &h->ev_in_free, &h->ev_state, &h->ev_rec, &h->ev_snap[0], &h->ev_snap[1]};
   for (cudaEvent_t* ev : evs)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -93,8 +95,8 @@ void swgb::release_io(sw_handle* h) {
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
   h->ev_in_done = h->ev_in_free = h->ev_state = h->ev_rec = h->ev_snap[0] = h->ev_snap[1] = nullptr;
-  cudaFree(h->stage_in);
-  cudaFree(h->snap);
+  swgb::dev_free(h->stage_in, h->stream);
+  swgb::dev_free(h->snap, h->stream);
   h->stage_in = h->snap = nullptr;
   h->io_buf[0] = h->io_buf[1] = nullptr;
   h->snap_wait[0] = h->snap_wait[1] = false;

@@ -258,6 +258,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
   __syncthreads();
 
   // ---- phase 2: unions of runs joined by in-tile +y / +z bonds
+  const uint32_t cap = lat.cap;
   if (rowv) {
     if (Y) {
       const int rn = r + (y1 - y);
@@ -266,7 +267,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
       while (U) {
         const int b = __ffs(U) - 1;
         U &= U - 1u;
-        sunion(par, (uint32_t)(32 * r) + run_start(S, b), (uint32_t)(32 * rn) + run_start(Sn, b), lat.err);
+        sunion(par, (uint32_t)(32 * r) + run_start(S, b), (uint32_t)(32 * rn) + run_start(Sn, b), lat.err, cap);
       }
     }
     if (D == 3 && Z) {
@@ -276,10 +277,10 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
       while (U) {
         const int b = __ffs(U) - 1;
         U &= U - 1u;
-        sunion(par, (uint32_t)(32 * r) + run_start(S, b), (uint32_t)(32 * rn) + run_start(Sn, b), lat.err);
+        sunion(par, (uint32_t)(32 * r) + run_start(S, b), (uint32_t)(32 * rn) + run_start(Sn, b), lat.err, cap);
       }
     }
-    if (XW) sunion(par, (uint32_t)(32 * r) + run_start(S, L - 1), (uint32_t)(32 * r), lat.err);
+    if (XW) sunion(par, (uint32_t)(32 * r) + run_start(S, L - 1), (uint32_t)(32 * r), lat.err, cap);
   }
   __syncthreads();
 

@@ -8,7 +8,6 @@
 // forest and an error flag) in a fixed array of this library's module,
 // instead of a buffer allocated per handle.
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "../../include/sw.h"
@@ -22,32 +21,21 @@ namespace {
 constexpr uint32_t kNoallocWords = SW_NOALLOC_MAX_SITES + 64u;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-uint32_t* g_scratch_ptr[kMaxDevices] = {};
-
 int noalloc_fail(int code, const std::string& msg) {
   swgb::set_last_error(msg);
   return code;
 }
 
 // Device address of the scratch array on the current device.  The host-side
-// name g_noalloc_scratch is only a stand-in; the address is looked up once
-// per device with that device current.
+// name g_noalloc_scratch is only a stand-in; the address is looked up on
+// every call, with the caller's device current, so that it stays valid
+// after a cudaDeviceReset (which reloads the module at a new address).
 int scratch_for_current_device(uint32_t** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(SW_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SW_ERR_CUDA, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return noalloc_fail(SW_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return noalloc_fail(SW_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = static_cast<uint32_t*>(p);
   return SW_OK;
 }
 
@@ -66,11 +54,19 @@ int sw_label_from_bonds_noalloc(int dim, int L, const uint32_t* dev_mask, int32_
   if (n > (double)SW_NOALLOC_MAX_SITES)
     return noalloc_fail(SW_ERR_BAD_ARG, "lattice too large for the no-allocation scratch: L^dim must be <= " +
                                             std::to_string(SW_NOALLOC_MAX_SITES) + " sites");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the call reads its error flag back and synchronises the stream, which a
+  // stream capture does not allow: refuse before any GPU work
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+  if (ce != cudaSuccess)
+    return noalloc_fail(SW_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+  if (cs != cudaStreamCaptureStatusNone)
+    return noalloc_fail(SW_ERR_BAD_ARG, "label_from_bonds_noalloc cannot run inside a stream capture");
   uint32_t* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != SW_OK) return rc;
 
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   swgb::Lattice lat{};
   lat.N = (uint32_t)n;
   lat.L = L;
@@ -87,6 +83,7 @@ int sw_label_from_bonds_noalloc(int dim, int L, const uint32_t* dev_mask, int32_
   lat.model = swgb::kIsing;
   lat.hooked = nullptr;   // labeling only: the merge keeps no hooked lists
   lat.nhooked = nullptr;
+  lat.cap = swgb::kLoopCap;
 
   int flag = 0;
   cudaError_t e = cudaMemsetAsync(lat.err, 0, sizeof(int), st);  // the flag must start at zero

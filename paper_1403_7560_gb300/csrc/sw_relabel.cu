@@ -68,16 +68,16 @@ __global__ void __launch_bounds__(kT) k_le_scan(Lattice lat, int32_t* label, int
   }
 }
 
-__global__ void __launch_bounds__(kT) k_le_analysis(uint32_t N, int32_t* label, int* err) {
+__global__ void __launch_bounds__(kT) k_le_analysis(uint32_t N, int32_t* label, int* err, uint32_t cap) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     int32_t r = __ldcg(&label[i]);
-    int it = 0;
-    for (; it < (1 << 22); ++it) {
+    uint32_t it = 0;
+    for (; it < cap; ++it) {
       const int32_t p = __ldcg(&label[r]);
       if (p == r) break;
       r = p;
     }
-    if (it == (1 << 22)) atomicExch(err, kErrTimeout);
+    if (it == cap) atomicExch(err, kErrTimeout);
     label[i] = r;
   }
 }
@@ -102,7 +102,7 @@ extern "C" int sw_relabel(sw_handle* h, int method, int32_t* host_labels, float*
   const swgb::Lattice& lat = h->lat;
   cudaStream_t st = h->stream;
   cudaError_t e = cudaSuccess;
-  if (!h->d_labels) e = cudaMalloc(&h->d_labels, (size_t)lat.N * 4);
+  if (!h->d_labels) e = swgb::dev_alloc((void**)&h->d_labels, (size_t)lat.N * 4, st);
   int* d_flag = nullptr;
   int* h_flag = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -111,6 +111,7 @@ extern "C" int sw_relabel(sw_handle* h, int method, int32_t* host_labels, float*
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   int iters = 0;
+  bool timed_out = false;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) {
@@ -123,18 +124,26 @@ extern "C" int sw_relabel(sw_handle* h, int method, int32_t* host_labels, float*
       iters = 1;
     } else {
       swgb::k_le_init<<<swgb::grid(lat.N), swgb::kT, 0, st>>>(lat.N, h->d_labels);
-      const int cap = (int)(lat.N < 1000000u ? lat.N + 2 : 1000000u);
-      for (iters = 0; iters < cap && e == cudaSuccess;) {
+      // at most N + 1 scans change a label (each lowers one); the handle's
+      // loop cap can lower the limit further
+      uint32_t cap = lat.N < 1000000u ? lat.N + 2u : 1000000u;
+      if (lat.cap < cap) cap = lat.cap;
+      bool converged = false;
+      for (iters = 0; (uint32_t)iters < cap && e == cudaSuccess;) {
         e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
         if (lat.dim == 2) swgb::k_le_scan<2><<<swgb::grid(lat.N), swgb::kT, 0, st>>>(lat, h->d_labels, d_flag);
         else swgb::k_le_scan<3><<<swgb::grid(lat.N), swgb::kT, 0, st>>>(lat, h->d_labels, d_flag);
-        swgb::k_le_analysis<<<swgb::grid(lat.N), swgb::kT, 0, st>>>(lat.N, h->d_labels, lat.err);
+        swgb::k_le_analysis<<<swgb::grid(lat.N), swgb::kT, 0, st>>>(lat.N, h->d_labels, lat.err, lat.cap);
         ++iters;
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess && *h_flag == 0) break;
+        if (e == cudaSuccess && *h_flag == 0) {
+          converged = true;
+          break;
+        }
       }
+      if (e == cudaSuccess && !converged) timed_out = true;
     }
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -153,5 +162,10 @@ extern "C" int sw_relabel(sw_handle* h, int method, int32_t* host_labels, float*
   }
   if (ms) *ms = t;
   if (iterations) *iterations = iters;
-  return sw_sync(h);
+  const int rc = sw_sync(h);
+  if (rc == SW_OK && timed_out) {
+    swgb::set_last_error("label equivalence: the iteration cap was reached before convergence");
+    return SW_ERR_TIMEOUT;
+  }
+  return rc;
 }

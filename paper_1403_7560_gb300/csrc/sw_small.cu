@@ -138,7 +138,8 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
       const uint32_t A0 = pl[g], X = A0 & (vmask >> 1), S = ss[g], base = row * L + x0;
       if ((A0 >> (nvalid - 1)) & 1u) {
         const uint32_t i = base + (uint32_t)(nvalid - 1);
-        sunion(par, base + run_start(S, nvalid - 1), x0 + (uint32_t)nvalid == L ? row * L : i + 1u, lat.err);
+        sunion(par, base + run_start(S, nvalid - 1), x0 + (uint32_t)nvalid == L ? row * L : i + 1u, lat.err,
+               lat.cap);
       }
 #pragma unroll
       for (int d = 1; d < D; ++d) {
@@ -151,7 +152,7 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
         while (U) {
           const int b = __ffs(U) - 1;
           U &= U - 1u;
-          sunion(par, base + run_start(S, b), basen + run_start(Sn, b), lat.err);
+          sunion(par, base + run_start(S, b), basen + run_start(Sn, b), lat.err, lat.cap);
         }
       }
     }

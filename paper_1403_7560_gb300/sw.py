@@ -49,6 +49,7 @@ _SIGNATURES = {
     "sw_discard": (_i, [_vp, _i]),
     "sw_measure": (_i, [_vp, ctypes.POINTER(sw_moments)]),
     "sw_sync": (_i, [_vp]),
+    "sw_set_loop_cap": (_i, [_vp, ctypes.c_longlong]),
     "sw_set_stream": (_i, [_vp, _vp]),
     "sw_sweep_counter": (_u64, [_vp]),
     "sw_set_sweep_counter": (_i, [_vp, _u64]),
@@ -162,6 +163,10 @@ def sw_measure(h: Handle) -> dict:
     m = sw_moments()
     _check(lib().sw_measure(h, ctypes.byref(m)))
     return {f: getattr(m, f) for f, _ in sw_moments._fields_}
+
+
+def sw_set_loop_cap(h: Handle, cap: int):
+    _check(lib().sw_set_loop_cap(h, int(cap)))
 
 
 def sw_sync(h: Handle):

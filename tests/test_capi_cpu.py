@@ -74,6 +74,7 @@ def test_null_handle_calls_fail_cleanly(swlib):
     assert lib.sw_batch_get_config(None, None, None, None, None) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_batch_autotune(None, 1, None) == swlib.SW_ERR_BAD_ARG
     assert lib.sw_set_sweep_target(None, 5) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_set_loop_cap(None, 0) == swlib.SW_ERR_BAD_ARG
     lib.sw_destroy(None)
     assert swlib.sw_series_capacity() >= 1024
 
@@ -104,3 +105,37 @@ def test_device_bytes_accounting(swlib):
     assert db(swlib.SW_ISING, 2, 64, 2) < db(swlib.SW_ISING, 2, 128, 2) < db(swlib.SW_ISING, 2, 256, 2)
     for bad in ((9, 2, 16, 2), (0, 4, 16, 2), (0, 2, 3, 2), (0, 3, 2000, 2)):
         assert db(*bad) == 0
+
+
+@pytest.mark.parametrize("dim,L,mask,labels,needle", [
+    (1, 16, 1, 1, "dim"), (4, 16, 1, 1, "dim"), (2, 3, 1, 1, "L must"),
+    (2, 16, 0, 1, "NULL"), (2, 16, 1, 0, "NULL"),
+    (3, 129, 1, 1, "too large"),                   # 129^3 = 2,146,689 > 2^21 sites
+    (2, 1449, 1, 1, "too large"),                  # 1449^2 = 2,099,601 > 2^21 sites
+])
+def test_noalloc_rejects_bad_arguments_before_any_gpu_work(swlib, dim, L, mask, labels, needle):
+    """sw_label_from_bonds_noalloc validates dim, L, its buffers and the
+    scratch limit before any CUDA call, so it fails cleanly on a machine
+    without a GPU (the pointers are never dereferenced)."""
+    lib = swlib.lib()
+    rc = lib.sw_label_from_bonds_noalloc(dim, L, 16 if mask else None, 16 if labels else None, None)
+    assert rc == swlib.SW_ERR_BAD_ARG
+    assert needle in swlib.sw_last_error()
+
+
+def test_noalloc_limit_is_exact(swlib):
+    """The scratch holds 2^21 sites: 128^3 (exactly 2^21) and 1448^2 fit,
+    the next cube and square do not and are refused on the host."""
+    lib = swlib.lib()
+    assert 128 ** 3 <= swlib.SW_NOALLOC_MAX_SITES < 129 ** 3
+    assert 1448 ** 2 <= swlib.SW_NOALLOC_MAX_SITES < 1449 ** 2
+    assert lib.sw_label_from_bonds_noalloc(3, 129, 16, 16, None) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_label_from_bonds_noalloc(2, 1449, 16, 16, None) == swlib.SW_ERR_BAD_ARG
+
+
+def test_loop_cap_argument_range(swlib):
+    """sw_set_loop_cap refuses a NULL handle and caps above the production
+    cap; it needs no GPU to check either."""
+    lib = swlib.lib()
+    assert lib.sw_set_loop_cap(None, -1) == swlib.SW_ERR_BAD_ARG
+    assert lib.sw_set_loop_cap(None, 1 << 23) == swlib.SW_ERR_BAD_ARG

@@ -203,6 +203,7 @@ def test_config_2d_ising_L64_full_run(sw):
         assert np.array_equal(sw.sw_get_labels(h), o.labels)
     finally:
         sw.sw_destroy(h)
+        o.close()
 
 
 def test_config_3d_ising_L256_first_sweeps(sw):
@@ -211,6 +212,98 @@ def test_config_3d_ising_L256_first_sweeps(sw):
     records)."""
     model, dim, L, q, T, seed, _, _ = inputs.WORKLOADS["ising3d_L256"]
     run_exact_parity(sw, model, dim, L, q, T, seed, sweeps=2)
+
+
+def test_config_3d_ising_L256_thermalised(sw):
+    """The benchmark's lattice in the regime it is timed in: 100 discarded
+    sweeps on the GPU from the seeded start (K = 0.2216546, clusters
+    spanning the lattice), then the oracle takes over the GPU's state and
+    sweep counter and both run 3 measured sweeps.  Bonds, labels, spins,
+    records and accumulators are bit-identical."""
+    model, dim, L, q, T, seed, ndisc, _ = inputs.WORKLOADS["ising3d_L256"]
+    h = sw.sw_create(model, dim, L, q, T, seed)
+    o = oracle.Oracle(model, dim, L, q, T, seed)
+    try:
+        sw.sw_discard(h, ndisc)
+        sw.sw_measure(h)
+        o.spins = sw.sw_get_spins(h)
+        o.sweep_counter = int(sw.sw_sweep_counter(h))
+        assert o.sweep_counter == ndisc
+        for k in range(ndisc + 1, ndisc + 4):
+            sw.sw_sweep(h, 1)
+            o.sweep(1)
+            assert np.array_equal(sw.sw_get_bonds(h), o.planes), f"bonds, sweep {k}"
+            lab = sw.sw_get_labels(h)
+            assert np.array_equal(lab, o.labels), f"labels, sweep {k}"
+            assert np.array_equal(sw.sw_get_spins(h), o.spins), f"spins, sweep {k}"
+            rec, ref = sw.sw_get_series(h, k, 1)[0], o.last_record()
+            for f in ("M", "E", "nclusters", "M2", "Ed"):
+                assert rec[f] == ref[f], (f, k, rec[f], ref[f])
+            # the regime of the benchmark: one cluster holds a sizeable share
+            assert np.bincount(lab).max() > 0.01 * lab.size, k
+        got, ref = sw.sw_measure(h), o.take_acc()
+        for f in ("n_sweeps", "sum_M2", "sum_M4", "sum_E", "sum_E2", "sum_nclusters"):
+            assert got[f] == ref[f], (f, got[f], ref[f])
+    finally:
+        sw.sw_destroy(h)
+        o.close()
+
+
+@pytest.mark.parametrize("model,dim,L,q,T", [
+    (ISING, 2, 48, 2, 2.269185), (ISING, 3, 40, 2, 4.5115), (POTTS, 3, 20, 3, 1.8),
+    (POTTS, 2, 70, 4, 0.910239), (CLOCK, 3, 12, 512, 2.2)])
+def test_derived_moments_follow_their_definitions(sw, model, dim, L, q, T):
+    """sw_measure's derived values are the definitions applied to the
+    accumulators, which equal the oracle's bit for bit: U = <M^4>/<M^2>^2
+    (Sec. 3), e = <E>/N, C/N = (<E^2> - <E>^2)/(N T^2), mean cluster size
+    = N/<clusters>; each compared exactly (the same double operations)."""
+    h = sw.sw_create(model, dim, L, q, T, 515)
+    o = oracle.Oracle(model, dim, L, q, T, 515)
+    try:
+        sw.sw_discard(h, 20)
+        o.sweep(20, measure=False)
+        sw.sw_measure(h)
+        o.take_acc()
+        sw.sw_sweep(h, 60)
+        o.sweep(60)
+        got, acc = sw.sw_measure(h), o.take_acc()
+        for f in acc:
+            assert got[f] == acc[f], f
+        n, N = acc["n_sweeps"], float(L ** dim)
+        m2, m4 = acc["sum_M2"] / n, acc["sum_M4"] / n
+        e1, e2 = acc["sum_E"] / n, acc["sum_E2"] / n
+        assert got["U"] == m4 / (m2 * m2)
+        assert got["e_per_spin"] == e1 / N
+        assert got["c_per_spin"] == (e2 - e1 * e1) / (N * T * T)
+        assert got["mean_cluster_size"] == N / (acc["sum_nclusters"] / n)
+        assert 1.0 <= got["U"] and 1.0 <= got["mean_cluster_size"] <= N and got["c_per_spin"] >= 0.0
+    finally:
+        sw.sw_destroy(h)
+        o.close()
+
+
+def test_derived_moments_xy_and_limits(sw):
+    """XY: the same definitions on the GPU's own accumulators; no bonds at
+    T -> infinity give a mean cluster size of exactly 1."""
+    h = sw.sw_create(XY, 3, 16, 2, 2.2, 9)
+    try:
+        sw.sw_sweep(h, 40)
+        got = sw.sw_measure(h)
+        n, N, T = got["n_sweeps"], 16.0 ** 3, 2.2
+        m2, m4 = got["sum_M2"] / n, got["sum_M4"] / n
+        e1, e2 = got["sum_E"] / n, got["sum_E2"] / n
+        assert got["U"] == m4 / (m2 * m2)
+        assert got["e_per_spin"] == e1 / N
+        assert got["c_per_spin"] == (e2 - e1 * e1) / (N * T * T)
+        assert got["mean_cluster_size"] == N / (got["sum_nclusters"] / n)
+    finally:
+        sw.sw_destroy(h)
+    h = sw.sw_create(ISING, 2, 64, 2, 1e9, 9)
+    try:
+        sw.sw_sweep(h, 5)
+        assert sw.sw_measure(h)["mean_cluster_size"] == 1.0
+    finally:
+        sw.sw_destroy(h)
 
 
 @pytest.mark.parametrize("dim,L,T", [(3, 1024, 1 / 0.2216546), (2, 32768, 2.269185)])
@@ -317,7 +410,8 @@ def xy_borderline(model_T, dim, L, seed, k, theta, gpu_mask, ora_mask):
         p = np.where(prod > 0, -np.expm1(-2.0 / model_T * prod), 0.0)
         w = np.array([oracle.philox([int(i), k, 1, 0], [seed & 0xffffffff, seed >> 32])[d] for i in idx])
         u = (w >> 8).astype(np.float64) * 2.0 ** -24
-        assert np.all(np.abs(u - p) < 1e-5) or np.all(np.abs(prod) < 1e-5), (u, p, prod)
+        near = (np.abs(u - p) < 1e-5) | (np.abs(prod) < 1e-5)
+        assert np.all(near), (u[~near], p[~near], prod[~near])
         n += idx.size
     return n
 
@@ -354,30 +448,45 @@ def test_xy_sweeps(sw, dim, L, T, sweeps):
         sw.sw_destroy(h)
 
 
-def test_xy_config_3d_L256_one_sweep(sw):
+@pytest.mark.parametrize("ndisc", [0, 30])
+def test_xy_config_3d_L256(sw, ndisc):
+    """3D XY L=256 at K = 0.4541652, from the seeded start and after 30
+    discarded sweeps: every bond that differs from the oracle's lies at the
+    rounding edge of its probability (checked bit by bit), labels equal the
+    oracle's on the GPU's mask, angles agree within 1e-5 rad, and the
+    record's moments within the float summation bound."""
     model, dim, L, q, T, seed, _, _ = inputs.WORKLOADS["xy3d_L256"]
+    N = L ** dim
     h = sw.sw_create(model, dim, L, q, T, seed)
     try:
+        sw.sw_discard(h, ndisc)
         theta = sw.sw_get_spins(h)
-        sw.sw_sweep(h, 1)
-        gmask = sw.sw_get_bonds(h)
-        glab = sw.sw_get_labels(h)
-        gnew = sw.sw_get_spins(h)
-        omask = oracle.bonds(XY, dim, L, 2, T, seed, 1, theta)
-        diff = int(np.unpackbits((gmask ^ omask).view(np.uint8)).sum())
-        assert diff <= 200
-        assert np.array_equal(glab, oracle.labels(dim, L, gmask))
-        onew, _ = oracle.flip(XY, dim, L, 2, seed, 1, glab, theta)
-        assert ang_diff(gnew, onew).max() < ANGLE_TOL
+        for k in range(ndisc + 1, ndisc + 3):
+            sw.sw_sweep(h, 1)
+            gmask = sw.sw_get_bonds(h)
+            glab = sw.sw_get_labels(h)
+            gnew = sw.sw_get_spins(h)
+            omask = oracle.bonds(XY, dim, L, 2, T, seed, k, theta)
+            xy_borderline(T, dim, L, seed, k, theta, gmask, omask)
+            assert np.array_equal(glab, oracle.labels(dim, L, gmask)), k
+            onew, ncl = oracle.flip(XY, dim, L, 2, seed, k, glab, theta)
+            assert ang_diff(gnew, onew).max() < ANGLE_TOL, k
+            rec = sw.sw_get_series(h, k, 1)[0]
+            ref = oracle.moments(XY, dim, L, 2, gnew)
+            tol = 2e-6 * N * (dim + 1) + 1e-3
+            assert abs(rec["mx"] - ref["mx"]) < tol and abs(rec["my"] - ref["my"]) < tol, k
+            assert abs(rec["e_xy"] - ref["e_xy"]) < tol and rec["nclusters"] == ncl, k
+            theta = gnew
     finally:
         sw.sw_destroy(h)
 
 
-def test_xy_ensemble_moments_within_3_sigma(sw):
-    """Independent GPU and oracle XY runs (2D L=16, T=0.9): binned means of
-    E and M^2 agree within 3 combined standard errors (plus 1% slack)."""
-    dim, L, T = 2, 16, 0.9
-    bins, per = 20, 2000
+@pytest.mark.parametrize("dim,L,T,bins,per", [(2, 16, 0.9, 20, 2000), (3, 8, 2.2, 20, 2000)])
+def test_xy_ensemble_moments_within_3_sigma(sw, dim, L, T, bins, per):
+    """Independent GPU and oracle XY runs (different seeds): binned means of
+    E and M^2 agree within 3 combined standard errors.  Each bin averages
+    2000 sweeps, far longer than the SW autocorrelation time at these sizes,
+    so the bins are independent and their spread gives the error."""
 
     def binned(step_measure):
         rows = []
@@ -405,9 +514,10 @@ def test_xy_ensemble_moments_within_3_sigma(sw):
         gm, ge = binned(g)
         cm, ce = binned(c)
         for j in range(2):
-            assert abs(gm[j] - cm[j]) < 3 * math.hypot(ge[j], ce[j]) + 0.01 * abs(cm[j]), (j, gm, cm, ge, ce)
+            assert abs(gm[j] - cm[j]) < 3 * math.hypot(ge[j], ce[j]), (j, gm, cm, ge, ce)
     finally:
         sw.sw_destroy(h)
+        o.close()
 
 
 # ---------------------------------------------------------------- API behaviour
@@ -455,5 +565,49 @@ def test_series_range_errors(sw):
         assert [r["sweep"] for r in sw.sw_get_series(h, 4, 2)] == [4, 5]
         with pytest.raises(sw.SwError):
             sw.sw_get_series(h, 6, 1)          # not done yet
+    finally:
+        sw.sw_destroy(h)
+
+
+# ---------------------------------------------------------------- failure detection
+def test_capped_loops_report_timeout_and_the_handle_recovers(sw):
+    """Failure detection without a GPU fault: with the handle's loop cap at
+    0 every union loop (shared-memory tile labeling, global merge), every
+    compression walk and every label-equivalence iteration gives up at once.
+    The kernels set the device error flag and return; the next synchronising
+    call reports SW_ERR_TIMEOUT.  With the production cap restored the same
+    handle labels correctly and sweeps bit-identically to the oracle."""
+    dim, L, T, seed = 2, 256, 2.269185, 3
+    N = L ** dim
+    h = sw.sw_create(ISING, dim, L, 2, T, seed)
+    try:
+        on = inputs.pack_planes(np.ones((dim, N), bool), dim, L)
+        sw.sw_set_loop_cap(h, 0)
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_label_from_bonds(h, on)
+        assert e.value.code == sw.SW_ERR_TIMEOUT
+        sw.sw_sweep(h, 2)
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_sync(h)
+        assert e.value.code == sw.SW_ERR_TIMEOUT
+        with pytest.raises(sw.SwError) as e:
+            sw.sw_relabel(h, sw.SW_LABEL_EQUIVALENCE)
+        assert e.value.code == sw.SW_ERR_TIMEOUT
+        sw.sw_sync(h)                                   # the flag was cleared
+        sw.sw_set_loop_cap(h, -1)
+        assert (sw.sw_label_from_bonds(h, on) == 0).all()
+        # resume from a known state: the handle sweeps exactly as the oracle
+        o = oracle.Oracle(ISING, dim, L, 2, T, seed)
+        try:
+            sw.sw_set_spins(h, o.spins)
+            sw.sw_set_sweep_counter(h, 0)
+            sw.sw_measure(h)
+            for k in range(1, 4):
+                sw.sw_sweep(h, 1)
+                o.sweep(1)
+                assert np.array_equal(sw.sw_get_labels(h), o.labels), k
+                assert np.array_equal(sw.sw_get_spins(h), o.spins), k
+        finally:
+            o.close()
     finally:
         sw.sw_destroy(h)
