@@ -14,6 +14,13 @@ a barrier and torch.cuda.synchronize(); the max over ranks.  N > 1 runs N
 independent replicas (one lattice per GPU, seed 1001 + rank): the sweep of
 one lattice does not shard.  The reference arm times the CPU oracle (single
 thread) on the same workload, over a bounded number of sweeps.
+
+On one GPU the same line also carries the two serving workloads: `batch`
+(256 ragged 2D lattices advanced together, 500 sweeps) and `serve` (a mixed
+request stream with the full size ranges -- 2D L up to 4096, 3D L up to
+256, 100 to 5000 sweeps -- 48 jobs, served by continuous batching against
+one job at a time, with jobs/s and p50/p99 latency).  --headline-only skips
+them; --workload batch|serve runs one alone.
 """
 from __future__ import annotations
 
@@ -46,23 +53,53 @@ WORKLOAD = {"workload": "3D Ising SW sweep, simple cubic L=256 periodic, K=0.221
             "model": "ising", "dim": 3, "L": L, "sites": N_SITES, "T": T,
             "l2": "flushed between timed steps (512 MiB write)"}
 
-# Algorithmic bytes per site per sweep of each kernel (3D Ising), the
-# minimum each must move: bond+tile-label reads the spin (1 B) and writes
-# the bond bits (3/8 B) and the forest word (4 B); flip reads the forest
-# word (4 B) and writes the spin (1 B); measurement reads the spin (1 B).
-# The merge touches only tile faces and is given per face bond instead.
-KERNEL_BYTES_PER_SITE = {"bond_label": 1 + 3 / 8 + 4, "merge": None, "flip": 4 + 1, "measure": 1}
+# Bytes per site per sweep of each phase (3D Ising) in the reference bytes
+# model: bond (read the spin, 1 B; write the bond bits, 3/8 B) plus tile
+# label (read the bond bits, 3/8 B; write the label, 4 B) for the fused
+# bond+label kernel; flip (read the label, 4 B; write the spin, 1 B);
+# measurement (read the spin, 1 B).  The merge touches tile faces only.
+KERNEL_BYTES_PER_SITE = {"bond_label": 1 + 3 / 8 + 3 / 8 + 4, "merge": None, "flip": 4 + 1, "measure": 1}
 PHASES = ["bond_label", "merge", "flip", "measure"]
-# DRAM bytes (read + write) of one launch of the dominant kernel, k_label
-# with measurement, from one ncu capture of this build (cold cache; see
-# profiles/sweep_kernels_ising3d_L256.md); None once that kernel changes.
-KERNEL_DRAM_BYTES = {"bond_label": 16.847104e6 + 12.827648e6}
+# The committed ncu summary of the dominant kernel carries its DRAM bytes
+# per launch, its limiter and a hash of the sources it was built from; the
+# figures are reported only while the sources still hash the same.
+KERNEL_PROFILE = os.path.join(ROOT, "profiles", "k_label_ising3d_L256.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1403_7560_gb300", "csrc", f)
+                  for f in ("sw_label.cu", "sw_device.cuh", "sw_internal.h")]
 # kernels one measured sweep launches: k_label (bonds + tile labels + the
 # previous sweep's measurement), k_merge, k_compress, k_apply
 KERNELS_PER_SWEEP = 4
 # Reference bytes model: 10.75 B/site/sweep for 3D Ising (bond 1.375,
 # tile label 4.375, flip 5), independent of the schedule.
 B_REF = 10.75
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_kernel():
+    """(DRAM bytes per launch, limiter, note) from the committed ncu summary
+    of the labeling kernel; None figures when the summary is missing or was
+    taken on other sources."""
+    fields = {}
+    try:
+        with open(KERNEL_PROFILE) as f:
+            for line in f:
+                line = line.strip().lstrip("-").strip()
+                for key in ("source_sha", "dram_bytes_per_launch", "limiter"):
+                    if line.startswith(key + ":"):
+                        fields[key] = line.split(":", 1)[1].strip().strip("`")
+    except OSError:
+        return None, None, "no committed ncu summary of the kernel"
+    if fields.get("source_sha") != kernel_source_hash():
+        return None, None, "the kernel's sources changed since the committed ncu capture"
+    return float(fields["dram_bytes_per_launch"]), fields.get("limiter"), None
 
 
 def peaks():
@@ -418,9 +455,16 @@ def run_gpu(args):
     e2e["synchronous"] = {"value": aggregate(world, N_SITES, sync_steps, sync_s), "steps": sync_steps,
                           "mode": "sw_set_spins + sw_sweep + sw_get_spins + sw_get_series per step"}
 
+    legs = {}
+    if world == 1 and not args.headline_only:
+        # the ragged batch and the served stream of the same build, one GPU
+        legs["batch"] = batch_leg(args, torch.cuda.Stream())   # graph capture needs a non-default stream
+        legs["serve"] = serve_leg(args)
+
     if rank == 0:
         peak, peak_kind = peaks()
         dom = int(np.argmax(phase_ms))
+        traffic, limiter, traffic_note = profiled_kernel() if PHASES[dom] == "bond_label" else (None, None, None)
         bps = KERNEL_BYTES_PER_SITE[PHASES[dom]] or 0.0
         achieved = bps * N_SITES / (phase_ms[dom] * 1e-3) / 1e9
         ms_per_step = 1e3 * total_s / args.steps
@@ -431,10 +475,9 @@ def run_gpu(args):
             "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
             "roofline": {"bound": "hbm", "kernel": PHASES[dom], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": KERNEL_DRAM_BYTES.get(PHASES[dom]),
+                         "traffic": traffic, "traffic_note": traffic_note,
                          "peak_source": f"{peak_kind} hbm_gbs",
-                         "limiter": "instruction issue (ncu: 68% issue active, 5.0 warp instr/site)",
-                         "bytes_per_site": bps},
+                         "limiter": limiter, "bytes_per_site": bps},
             "phase_ms": dict(zip(PHASES, [float(v) for v in phase_ms])),
             "update_only": {"value": update_only, "unit": UNIT},
             "labeling": labeling,
@@ -446,6 +489,7 @@ def run_gpu(args):
             "moments": {"U": moments["U"], "e_per_spin": moments["e_per_spin"],
                         "mean_cluster_size": moments["mean_cluster_size"]},
         }
+        line.update(legs)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sweeps)
             line["other_workloads"]["xy3d_L256"]["cpu_baseline"] = cpu_baseline_xy()
@@ -463,7 +507,8 @@ def _job_list(specs):
 
 def batch_launches(specs, schedule):
     """Kernels one batch sweep launches: the tiled members' labels (one
-    launch per model under schedule 0, one in all under schedule 1), merge,
+    launch per model under label layout 0, one in all under layout 1 -- bit 0
+    of the schedule), merge,
     compression and apply; one launch per model of the small members (2D
     Ising up to 4096 sites, 2D Potts up to 8192, 3D up to 1024); the step
     counter."""
@@ -471,7 +516,7 @@ def batch_launches(specs, schedule):
         return L ** d <= ((8192 if m == 1 else 4096) if d == 2 else 1024)
     tiled = {m for (m, d, L, _, _, _) in specs if not is_small(m, d, L)}
     small = {m for (m, d, L, _, _, _) in specs if is_small(m, d, L)}
-    labels = (len(tiled) if schedule == 0 else 1) if tiled else 0
+    labels = (len(tiled) if (schedule & 1) == 0 else 1) if tiled else 0
     return labels + (3 if tiled else 0) + len(small) + 1
 
 
@@ -514,18 +559,17 @@ def small_batch(sw, inputs, st, sweeps=50):
             "gpu_launches": batch_launches(specs, 0) * sweeps}
 
 
-def run_batch(args):
+def batch_leg(args, st):
     """Ragged batch of 256 2D Ising/Potts lattices (seed 1003), advanced
-    together (one launch per phase, graph-replayed sweeps) vs the same
-    lattices swept one at a time.  Inputs total ~1 GB (larger than L2)."""
+    together (one launch per phase, graph-replayed sweeps, autotuned tile
+    shape, label layout and grid form) vs the same lattices swept one at a
+    time.
+    Inputs total ~1 GB (larger than L2)."""
     import torch
     import inputs
-    from paper_1403_7560_gb300 import build, sw
-    build.build()
-    torch.cuda.set_device(0)
+    from paper_1403_7560_gb300 import sw
     specs = inputs.ragged_batch(256, 1003)
     sites = sum(L ** d for (_, d, L, _, _, _) in specs)
-    st = torch.cuda.Stream()
     hs = [sw.sw_create(m, d, L, q, T, seed) for (m, d, L, q, T, seed) in specs]
     b = sw.sw_batch_create(2)
     sw.sw_batch_set_stream(b, st.cuda_stream)
@@ -533,24 +577,24 @@ def run_batch(args):
         sw.sw_set_stream(h, st.cuda_stream)
         sw.sw_batch_add(b, h)
     sw.sw_batch_sweep(b, max(args.warmup, 3))
-    # untimed: every tile shape and label schedule on real sweeps of the batch
+    # untimed: every tile shape, label layout and grid form on real sweeps of the batch
     tune_ms = sw.sw_batch_autotune(b, 5)
     cfg = sw.sw_batch_get_config(b)
     sw.sw_batch_sweep(b, 1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(0)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.mark_start()
     e0.record(st)
-    sw.sw_batch_sweep(b, args.steps)
+    sw.sw_batch_sweep(b, args.batch_sweeps)
     e1.record(st)
     torch.cuda.synchronize()
     clocks.mark_stop()
     clk = clocks.stop()
     t_batch = e0.elapsed_time(e1) / 1e3
     sw.sw_batch_destroy(b)
-    # the plain path: each lattice alone, one after another, same sweeps
-    k_serial = min(args.steps, 50)
+    # the plain path: each lattice alone, one after another
+    k_serial = min(args.batch_sweeps, 50)
     e0.record(st)
     for h in hs:
         sw.sw_sweep(h, k_serial)
@@ -560,19 +604,18 @@ def run_batch(args):
     for h in hs:
         sw.sw_measure(h)
         sw.sw_destroy(h)
-    v_batch = sites * args.steps / (t_batch * 1e9)
+    v_batch = sites * args.batch_sweeps / (t_batch * 1e9)
     v_serial = sites * k_serial / (t_serial * 1e9)
     small = small_batch(sw, inputs, st)
-    line = {"metric": "ragged batch site-updates/ns (256 2D Ising/Potts lattices, L 32..1024)",
-            "value": v_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_batch / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
-            "data": "synthetic",
+    return {"metric": "ragged batch site-updates/ns (256 2D Ising/Potts lattices, L 32..1024)",
+            "value": v_batch, "unit": UNIT, "steps": args.batch_sweeps,
+            "ms_per_step": 1e3 * t_batch / args.batch_sweeps,
             "config": {"workload": "ragged batch: 256 2D lattices, model uniform over Ising / Potts q=3 "
                                    "/ Potts q=4, L uniform over {32,48,...,1024}, T in [0.8,1.2] Tc, "
-                                   "seed 1003, one measured sweep per step, CUDA-graph replay, "
-                                   "autotuned tile shape and label schedule",
-                       "sites": sites, "l2": "inputs larger than L2"},
+                                   f"seed 1003, {args.batch_sweeps} measured sweeps in one "
+                                   "sw_batch_sweep call, CUDA-graph replay, autotuned tile shape and "
+                                   "schedule (label layout, grid form)", "sites": sites,
+                       "l2": "inputs larger than L2"},
             "serial": {"value": v_serial, "unit": UNIT, "steps": k_serial,
                        "note": "each lattice alone with sw_sweep, one after another"},
             "speedup_vs_serial": v_batch / v_serial,
@@ -581,19 +624,26 @@ def run_batch(args):
                                                          for sc in range(tune_ms.shape[1]) if tune_ms[sh, sc] > 0},
                          "note": "5 timed sweeps per configuration, before the timed region"},
             "small_lattices": small,
-            "gpu_launches": batch_launches(specs, cfg["schedule"]) * args.steps, "clocks": clk}
+            "gpu_launches": batch_launches(specs, cfg["schedule"]) * args.batch_sweeps, "clocks": clk}
+
+
+def run_batch(args):
+    import torch
+    from paper_1403_7560_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    leg = batch_leg(args, torch.cuda.Stream())
+    line = dict(leg, n_gpus=1, warmup=max(args.warmup, 3), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="int8", data="synthetic")
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
+def serve_leg(args):
     """Served request stream (seed 1004): continuous batching vs the
     one-at-a-time plain path, at saturation (all queued at t = 0) and at
     0.7 of the serial capacity (Poisson arrivals)."""
-    import torch
     import inputs
-    from paper_1403_7560_gb300 import build, serve
-    build.build()
-    torch.cuda.set_device(0)
+    from paper_1403_7560_gb300 import serve
     kw = dict(max_L2=args.max_l2, max_L3=args.max_l3, sweeps=(100, args.max_sweeps))
     budget = int(args.budget_gb * (1 << 30))
 
@@ -603,23 +653,24 @@ def run_serve(args):
         done = srv.run(jobs, realtime=realtime)
         wall = time.perf_counter() - t0
         srv.close()
-        return serve.summary(done, wall)
+        out = serve.summary(done, wall)
+        out["rejected"] = len(srv.rejected)
+        return out
 
     def serial(jobs, realtime):
         t0 = time.perf_counter()
         done = serve.run_serial(jobs, realtime=realtime)
         return serve.summary(done, time.perf_counter() - t0)
 
-    # warm-up: build the kernels' first launches
-    served(_job_list(inputs.served_stream(6, 7, **kw)), False)
+    # warm-up: the kernels' first launches
+    served(_job_list(inputs.served_stream(6, 7, max_L2=256, max_L3=32, sweeps=(100, 200))), False)
     sat_srv = served(_job_list(inputs.served_stream(args.jobs, 1004, **kw)), False)
     sat_ser = serial(_job_list(inputs.served_stream(args.jobs, 1004, **kw)), False)
     rate = 0.7 * sat_ser["jobs_per_s"]
     lat_srv = served(_job_list(inputs.served_stream(args.jobs, 1004, rate=rate, **kw)), True)
     lat_ser = serial(_job_list(inputs.served_stream(args.jobs, 1004, rate=rate, **kw)), True)
-    line = {"metric": "served mix jobs/s, p50/p99", "value": sat_srv["jobs_per_s"], "unit": "jobs/s",
-            "n_gpus": 1, "steps": args.jobs, "warmup": 1, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int8/uint8/f32", "data": "synthetic",
+    return {"metric": "served mix jobs/s, p50/p99", "value": sat_srv["jobs_per_s"], "unit": "jobs/s",
+            "steps": args.jobs,
             "config": {"workload": f"served stream, seed 1004, {args.jobs} jobs, class uniform over "
                                    "2D Ising / 3D Ising / 2D Potts q=3,4,8 / 3D XY, L log-uniform in "
                                    f"[16,{args.max_l2}] (2D) or [16,{args.max_l3}] (3D), T = Tc(1+U(-0.02,0.02)), "
@@ -629,6 +680,15 @@ def run_serve(args):
                            "speedup": sat_srv["jobs_per_s"] / sat_ser["jobs_per_s"]},
             "latency_at_0.7_serial_capacity": {"rate_jobs_per_s": rate, "served": lat_srv,
                                                "serial": lat_ser}}
+
+
+def run_serve(args):
+    import torch
+    from paper_1403_7560_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    line = dict(serve_leg(args), n_gpus=1, warmup=1, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="int8/uint8/f32", data="synthetic")
     print(json.dumps(line), flush=True)
 
 
@@ -643,10 +703,13 @@ def main():
     ap.add_argument("--workload", default="ising3d_L256", choices=["ising3d_L256", "batch", "serve"],
                     help="the headline 3D Ising L=256 sweep (default), the ragged batch, or the "
                          "served stream (one GPU)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the ragged-batch and served-stream legs of the default run")
+    ap.add_argument("--batch-sweeps", type=int, default=500, help="batch: measured sweeps")
     ap.add_argument("--jobs", type=int, default=48, help="serve: jobs in the stream")
-    ap.add_argument("--max-l2", type=int, default=1024, help="serve: largest 2D L")
-    ap.add_argument("--max-l3", type=int, default=128, help="serve: largest 3D L")
-    ap.add_argument("--max-sweeps", type=int, default=1000, help="serve: most sweeps of a job")
+    ap.add_argument("--max-l2", type=int, default=4096, help="serve: largest 2D L")
+    ap.add_argument("--max-l3", type=int, default=256, help="serve: largest 3D L")
+    ap.add_argument("--max-sweeps", type=int, default=5000, help="serve: most sweeps of a job")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="serve: HBM budget")
     ap.add_argument("--chunk", type=int, default=64, help="serve: sweeps per engine iteration")
     args = ap.parse_args()

@@ -155,6 +155,15 @@ int sw_measure(sw_handle* h, sw_moments* out);
 /* Synchronise the handle's stream and report any device error flag. */
 int sw_sync(sw_handle* h);
 
+/* Non-blocking completion test of the work enqueued so far on the handle's
+ * stream: 1 if all of it has completed, 0 if some is still running, a
+ * negative sw_status on error (SW_ERR_BAD_ARG for NULL, SW_ERR_CUDA).  It
+ * neither waits nor reads the device error flag (sw_sync does both).  A
+ * serving loop polls it to advance each lattice as soon as its previous
+ * chunk of sweeps is done.  sw_batch_query (below) does the same for a
+ * batch's stream. */
+int sw_query(sw_handle* h);
+
 /* Failure-detection hook (no counterpart in the paper).  Every device loop
  * whose trip count depends on the data -- the union retries of the tile
  * labeling (shared memory) and of the global merge, the compression and
@@ -282,6 +291,8 @@ size_t sw_series_capacity(void);
  *                          SW_ERR_BAD_ARG).  Single-lattice calls ignore it.
  *                          A serving loop gives each job its sweep count and
  *                          advances the whole batch by a fixed chunk.
+ * sw_batch_query(b)        1 if the batch's enqueued sweeps have completed,
+ *                          0 if not (non-blocking; see sw_query).
  * sw_batch_set_stream      run on a caller's non-default stream instead.
  * sw_batch_size            number of members.
  * sw_batch_destroy(b)      frees the batch (not its members).  sw_destroy of a
@@ -294,11 +305,15 @@ size_t sw_series_capacity(void);
  * one CTA (a thread per 32-site row word) per tile, in one of
  * SW_BATCH_TILE_SHAPES shapes: 2D 32x256, 32x128, 32x64; 3D 32x16x16,
  * 32x16x8, 32x8x8 (single lattices use 32x128 in 2D, shape 1, and
- * 32x16x16 in 3D, shape 0, which a new batch starts with).  The label schedule
- * is 0 (the Ising tiles in one launch with the two-state layout, the Potts
- * tiles in another) or 1 (all tiles in one launch, the Potts layout).  No
+ * 32x16x16 in 3D, shape 0, which a new batch starts with).  The schedule
+ * (0 .. SW_BATCH_SCHEDULES - 1) has two bits.  Bit 0 is the label layout: 0
+ * runs the Ising tiles in one launch with the two-state layout and the Potts
+ * tiles in another, 1 runs all tiles in one launch with the Potts layout.
+ * Bit 1 is the grid form of every phase (labels, merge, compression, apply):
+ * 0 launches one CTA per tile, 1 launches a persistent grid -- the SM count
+ * times the CTAs one SM holds -- whose CTAs stride over the tile map.  No
  * configuration changes any result: bonds, draws and canonical labels are
- * keyed by row word and site index, not by tile.
+ * keyed by row word and site index, not by tile or CTA.
  * sw_batch_set_config(b, shape, schedule)   selects one (SW_ERR_BAD_ARG out
  *                          of range); the next sweep recaptures the graph.
  * sw_batch_get_config(b, &shape, &schedule, &tile_y, &tile_z)   the current
@@ -309,24 +324,26 @@ size_t sw_series_capacity(void);
  *                          upload), then `sweeps` sweeps timed with CUDA
  *                          events (a host wait).  These are real measured
  *                          sweeps of every member, as sw_batch_sweep's: with
- *                          C = 3 shapes x (2 schedules if the batch holds both
- *                          Ising and Potts lattices, else 1), every counter
- *                          advances by C * (sweeps + 1).  ms (NULL or
- *                          SW_BATCH_TILE_SHAPES * SW_BATCH_LABEL_SCHEDULES
- *                          floats, index shape * 2 + schedule) receives the
+ *                          C = 3 shapes x 2 grid forms x (2 label layouts
+ *                          if the batch holds both Ising and Potts lattices,
+ *                          else 1), every counter advances by
+ *                          C * (sweeps + 1).  ms (NULL or
+ *                          SW_BATCH_TILE_SHAPES * SW_BATCH_SCHEDULES floats,
+ *                          index shape * 4 + schedule) receives the
  *                          time per sweep of each configuration, -1 where not
  *                          tried.  An empty batch returns SW_OK untouched;
  *                          sweeps < 1, or a member whose sweep target lies
  *                          within the C * (sweeps + 1) sweeps, is
  *                          SW_ERR_BAD_ARG. */
 #define SW_BATCH_TILE_SHAPES 3
-#define SW_BATCH_LABEL_SCHEDULES 2
+#define SW_BATCH_SCHEDULES 4
 typedef struct sw_batch sw_batch;
 sw_batch* sw_batch_create(int dim);
 void sw_batch_destroy(sw_batch* b);
 int sw_batch_add(sw_batch* b, sw_handle* h);
 int sw_batch_remove(sw_batch* b, sw_handle* h);
 int sw_batch_sweep(sw_batch* b, int n);
+int sw_batch_query(sw_batch* b);
 int sw_batch_set_stream(sw_batch* b, void* stream);
 size_t sw_batch_size(sw_batch* b);
 size_t sw_device_bytes(int model, int dim, int L, int q);

@@ -20,7 +20,7 @@
 using swgb::BatchMember;
 using swgb::BatchView;
 
-static_assert(SW_BATCH_TILE_SHAPES == swgb::kTileShapes && SW_BATCH_LABEL_SCHEDULES == swgb::kLabelSchedules,
+static_assert(SW_BATCH_TILE_SHAPES == swgb::kTileShapes && SW_BATCH_SCHEDULES == swgb::kBatchSchedules,
               "configuration counts of the public header");
 
 struct sw_batch {
@@ -38,7 +38,7 @@ struct sw_batch {
   uint32_t ntiles = 0;
   uint32_t ising_tiles = 0;           // the tile map lists the Ising members' tiles first
   int shape = 0;                      // tile shape (index into the shape table)
-  int schedule = 0;                   // label schedule (separate or one launch)
+  int schedule = 0;                   // label layout (bit 0) and grid form (bit 1)
   // small members (whole sweeps in one CTA's shared memory): member indices,
   // the Ising ones then the Potts ones, run on a forked branch of the graph
   uint32_t* d_small = nullptr;
@@ -194,8 +194,10 @@ int rebuild(sw_batch* b) {
       if (le == cudaSuccess && ntiles) {
         le = swgb::launch_label_batch(v, b->dim, b->shape, b->schedule, b->ising_tiles, b->ntiles - b->ising_tiles,
                                       b->stream);
-        if (le == cudaSuccess) le = swgb::launch_merge_batch(v, b->dim, b->shape, b->ntiles, b->stream);
-        if (le == cudaSuccess) le = swgb::launch_flip_batch(v, b->dim, b->shape, b->ntiles, b->stream);
+        if (le == cudaSuccess)
+          le = swgb::launch_merge_batch(v, b->dim, b->shape, b->schedule, b->ntiles, b->stream);
+        if (le == cudaSuccess)
+          le = swgb::launch_flip_batch(v, b->dim, b->shape, b->schedule, b->ntiles, b->stream);
       }
       if (le == cudaSuccess && nsmall) le = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
       if (le == cudaSuccess) le = swgb::launch_advance(v, b->stream);
@@ -290,6 +292,15 @@ int sw_batch_remove(sw_batch* b, sw_handle* h) {
 }
 
 size_t sw_batch_size(sw_batch* b) { return b ? b->members.size() : 0; }
+
+int sw_batch_query(sw_batch* b) {
+  if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
+  // the graph's side branch joins the batch stream, which therefore covers it
+  const cudaError_t e = cudaStreamQuery(b->stream);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return bcuda(e, "batch stream query");
+}
 
 int sw_batch_set_stream(sw_batch* b, void* stream) {
   if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
@@ -388,7 +399,7 @@ int sw_batch_sweep(sw_batch* b, int n) { return batch_sweep(b, n, nullptr); }
 int sw_batch_set_config(sw_batch* b, int shape, int schedule) {
   if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
   if (shape < 0 || shape >= swgb::kTileShapes) return bfail(SW_ERR_BAD_ARG, "tile shape out of range");
-  if (schedule < 0 || schedule >= swgb::kLabelSchedules) return bfail(SW_ERR_BAD_ARG, "label schedule out of range");
+  if (schedule < 0 || schedule >= swgb::kBatchSchedules) return bfail(SW_ERR_BAD_ARG, "schedule out of range");
   if (shape != b->shape || schedule != b->schedule) {
     cudaError_t e = cudaStreamSynchronize(b->stream);  // the replays in flight use the old tile map
     if (e != cudaSuccess) return bcuda(e, "batch sync");
@@ -411,15 +422,16 @@ int sw_batch_get_config(const sw_batch* b, int* shape, int* schedule, int* tile_
 int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep) {
   if (!b) return bfail(SW_ERR_BAD_ARG, "NULL batch");
   if (sweeps < 1) return bfail(SW_ERR_BAD_ARG, "sweeps < 1");
-  constexpr int kConfigs = swgb::kTileShapes * swgb::kLabelSchedules;
+  constexpr int kConfigs = swgb::kTileShapes * swgb::kBatchSchedules;
   if (ms_per_sweep)
     for (int c = 0; c < kConfigs; ++c) ms_per_sweep[c] = -1.0f;
   if (b->members.empty()) return SW_OK;
   bool ising = false, potts = false;
   for (const sw_handle* h : b->members) (h->model == SW_POTTS ? potts : ising) = true;
   // one label launch differs from two only when both kinds are present
-  const int schedules = (ising && potts) ? swgb::kLabelSchedules : 1;
-  const uint64_t total = (uint64_t)swgb::kTileShapes * schedules * ((uint64_t)sweeps + 1);
+  // (schedule bit 0); both grid forms are always tried (bit 1)
+  const bool both = ising && potts;
+  const uint64_t total = (uint64_t)swgb::kTileShapes * (both ? 4 : 2) * ((uint64_t)sweeps + 1);
   for (const sw_handle* h : b->members) {
     if (h->sweep + total >= 0xffffffffull) return bfail(SW_ERR_BAD_ARG, "sweep counter exhausted");
     // every configuration must time the same members
@@ -429,14 +441,15 @@ int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep) {
   int best_shape = b->shape, best_schedule = b->schedule;
   float best = -1.0f;
   for (int sh = 0; sh < swgb::kTileShapes; ++sh) {
-    for (int sc = 0; sc < schedules; ++sc) {
+    for (int sc = 0; sc < swgb::kBatchSchedules; ++sc) {
+      if ((sc & 1) && !both) continue;
       int rc = sw_batch_set_config(b, sh, sc);
       if (rc == SW_OK) rc = batch_sweep(b, 1, nullptr);  // graph capture and upload, untimed
       float ms = 0.0f;
       if (rc == SW_OK) rc = batch_sweep(b, sweeps, &ms);
       if (rc != SW_OK) return rc;
       ms /= (float)sweeps;
-      if (ms_per_sweep) ms_per_sweep[sh * swgb::kLabelSchedules + sc] = ms;
+      if (ms_per_sweep) ms_per_sweep[sh * swgb::kBatchSchedules + sc] = ms;
       if (best < 0.0f || ms < best) {
         best = ms;
         best_shape = sh;

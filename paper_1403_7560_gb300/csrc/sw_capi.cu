@@ -54,6 +54,18 @@ cudaError_t device_pool(cudaMemPool_t* out) {
 }
 }  // namespace
 
+int swgb::sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 1;
+    n = v;
+  }
+  return n;
+}
+
 cudaError_t swgb::dev_alloc(void** p, size_t bytes, cudaStream_t st) {
   *p = nullptr;
   cudaMemPool_t pool = nullptr;
@@ -455,6 +467,14 @@ int sw_sync(sw_handle* h) {
   const cudaError_t e = swgb::wait_io(h);
   if (e != cudaSuccess) return cuda_fail(e, "asynchronous I/O");
   return check_device_error(h);
+}
+
+int sw_query(sw_handle* h) {
+  if (!h) return fail(SW_ERR_BAD_ARG, "NULL handle");
+  const cudaError_t e = cudaStreamQuery(h->stream);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return cuda_fail(e, "stream query");
 }
 
 int sw_set_loop_cap(sw_handle* h, long long cap) {

@@ -127,14 +127,21 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, merge_blocks(Tile<D>::THREAD
   merge_tile<Tile<D>>(lat, blockIdx.x, sm);
 }
 
+// Batch kernels take tile-map entries t = blockIdx.x, blockIdx.x +
+// gridDim.x, ... below n: one per CTA when the grid covers the map, several
+// when it is a persistent grid of resident CTAs.
 template <class S>
-__global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_batch(BatchView bv) {
+__global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_batch(BatchView bv, uint32_t n) {
   __shared__ MergeSmem<S> sm;
   pdl_wait();
-  const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
-  if (*bv.step >= m.nsweeps) return;  // the member has had its sweeps this call
-  const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
-  merge_tile<S>(lat, __ldg(&bv.tile_index[blockIdx.x]), sm);
+  const uint32_t step = *bv.step;
+  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+    __syncthreads();  // the previous entry's readers of sm are done
+    const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
+    if (step >= m.nsweeps) continue;  // the member has had its sweeps this call
+    const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
+    merge_tile<S>(lat, __ldg(&bv.tile_index[t]), sm);
+  }
 }
 
 constexpr int kFlipThreads = 256, kFlipWarps = kFlipThreads / 32;
@@ -179,18 +186,20 @@ __global__ void __launch_bounds__(kFlipThreads, 8) k_compress(Lattice lat, Measu
 
 // Batch: one CTA per member tile; the CTA of each member's tile 0 first
 // writes that member's previous record (every step after the first).
-__global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv) {
+__global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv, uint32_t n) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
   pdl_wait();
-  const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
-  const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
   const uint32_t step = *bv.step;
-  if (step >= m.nsweeps) return;
-  const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
-  if (tile == 0u && (step > 0u || m.measure0))
-    finalize_record<kFlipWarps>(lat, m.meas, m.sweep0 + step, s_red, s_rd);
-  compress_tile(lat, tile);
+  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
+    const uint32_t tile = __ldg(&bv.tile_index[t]);
+    if (step >= m.nsweeps) continue;
+    const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
+    if (tile == 0u && (step > 0u || m.measure0))
+      finalize_record<kFlipWarps>(lat, m.meas, m.sweep0 + step, s_red, s_rd);
+    compress_tile(lat, tile);
+  }
 }
 
 // Every site takes its cluster's draw from its own word (local roots, now
@@ -269,16 +278,28 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
 // Batch apply: one CTA per member tile, warps over the tile's rows, lanes
 // over x; the member's model picks the state update.
 template <class S>
-__global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv) {
+__device__ __forceinline__ void apply_tile(const BatchMember& m, uint32_t tile, uint32_t step, long long* s_red);
+
+template <class S>
+__global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv, uint32_t n) {
+  __shared__ long long s_red[kFlipThreads / 32];
+  pdl_wait();
+  const uint32_t step = *bv.step;
+  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
+    if (step >= m.nsweeps) continue;
+    apply_tile<S>(m, __ldg(&bv.tile_index[t]), step, s_red);
+  }
+}
+
+// One member tile of the batch apply: warps over the tile's rows, lanes
+// over x; the member's model picks the state update; the tile's roots are
+// added to the member's cluster count.
+template <class S>
+__device__ __forceinline__ void apply_tile(const BatchMember& m, uint32_t tile, uint32_t step, long long* s_red) {
   constexpr int D = S::D, TY = S::TY, ROWS = S::ROWS, NW = kFlipThreads / 32, RPW = ROWS / NW;
   constexpr int B = 8;
   static_assert(RPW % B == 0, "whole batches of rows per warp");
-  __shared__ long long s_red[NW];
-  pdl_wait();
-  const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
-  const uint32_t tile = __ldg(&bv.tile_index[blockIdx.x]);
-  const uint32_t step = *bv.step;
-  if (step >= m.nsweeps) return;
   const Lattice lat = m.lat;  // a private copy: the spin stores cannot alias it
   const uint32_t sweep = m.sweep0 + step + 1u;
   const TileCoord tc = tile_coord<S>(lat, tile);
@@ -388,41 +409,50 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
 namespace {
 
 template <int D, int SH>
-cudaError_t merge_batch_shape(const BatchView& bv, uint32_t ntiles, cudaStream_t st) {
+cudaError_t merge_batch_shape(const BatchView& bv, uint32_t ntiles, bool persistent, cudaStream_t st) {
   using S = ShapeOf<D, SH>;
-  return launch_pdl(k_merge_batch<S>, ntiles, (unsigned)S::THREADS, st, bv);
+  const unsigned g = persistent ? batch_grid(k_merge_batch<S>, S::THREADS, ntiles) : ntiles;
+  return launch_pdl(k_merge_batch<S>, g, (unsigned)S::THREADS, st, bv, ntiles);
 }
 
 template <int D, int SH>
-cudaError_t flip_batch_shape(const BatchView& bv, uint32_t ntiles, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_compress_batch, ntiles, kFlipThreads, st, bv);
-  if (e == cudaSuccess) e = launch_pdl(k_apply_batch<ShapeOf<D, SH>>, ntiles, kFlipThreads, st, bv);
+cudaError_t flip_batch_shape(const BatchView& bv, uint32_t ntiles, bool persistent, cudaStream_t st) {
+  const unsigned gc = persistent ? batch_grid(k_compress_batch, kFlipThreads, ntiles) : ntiles;
+  const unsigned ga = persistent ? batch_grid(k_apply_batch<ShapeOf<D, SH>>, kFlipThreads, ntiles) : ntiles;
+  cudaError_t e = launch_pdl(k_compress_batch, gc, kFlipThreads, st, bv, ntiles);
+  if (e == cudaSuccess) e = launch_pdl(k_apply_batch<ShapeOf<D, SH>>, ga, kFlipThreads, st, bv, ntiles);
   return e;
 }
 
 template <int D>
-cudaError_t merge_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, cudaStream_t st) {
-  if (shape == 1) return merge_batch_shape<D, 1>(bv, ntiles, st);
-  if (shape == 2) return merge_batch_shape<D, 2>(bv, ntiles, st);
-  return merge_batch_shape<D, 0>(bv, ntiles, st);
+cudaError_t merge_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, bool persistent, cudaStream_t st) {
+  if (shape == 1) return merge_batch_shape<D, 1>(bv, ntiles, persistent, st);
+  if (shape == 2) return merge_batch_shape<D, 2>(bv, ntiles, persistent, st);
+  return merge_batch_shape<D, 0>(bv, ntiles, persistent, st);
 }
 
 template <int D>
-cudaError_t flip_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, cudaStream_t st) {
-  if (shape == 1) return flip_batch_shape<D, 1>(bv, ntiles, st);
-  if (shape == 2) return flip_batch_shape<D, 2>(bv, ntiles, st);
-  return flip_batch_shape<D, 0>(bv, ntiles, st);
+cudaError_t flip_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, bool persistent, cudaStream_t st) {
+  if (shape == 1) return flip_batch_shape<D, 1>(bv, ntiles, persistent, st);
+  if (shape == 2) return flip_batch_shape<D, 2>(bv, ntiles, persistent, st);
+  return flip_batch_shape<D, 0>(bv, ntiles, persistent, st);
 }
 
 }  // namespace
 
-cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st) {
+cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,
+                               cudaStream_t st) {
   static_assert(kTileShapes == 3, "one instantiation per shape");
-  return dim == 2 ? merge_batch_dim<2>(bv, shape, ntiles, st) : merge_batch_dim<3>(bv, shape, ntiles, st);
+  const bool persistent = (schedule & 2) != 0;
+  return dim == 2 ? merge_batch_dim<2>(bv, shape, ntiles, persistent, st)
+                  : merge_batch_dim<3>(bv, shape, ntiles, persistent, st);
 }
 
-cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st) {
-  return dim == 2 ? flip_batch_dim<2>(bv, shape, ntiles, st) : flip_batch_dim<3>(bv, shape, ntiles, st);
+cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,
+                              cudaStream_t st) {
+  const bool persistent = (schedule & 2) != 0;
+  return dim == 2 ? flip_batch_dim<2>(bv, shape, ntiles, persistent, st)
+                  : flip_batch_dim<3>(bv, shape, ntiles, persistent, st);
 }
 
 cudaError_t launch_advance(const BatchView& bv, cudaStream_t st) {

@@ -194,17 +194,39 @@ cudaError_t launch_measure(const Lattice& lat, int model, uint32_t sweep, const 
 cudaError_t launch_measure_rows(const Lattice& lat, uint32_t sweep, const Measure& m, cudaStream_t st);
 cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st);
 
-// Batched phases: one launch over every tile of every member (Ising/Potts,
-// one dimension, tile shape `shape`), then the step counter advances.
-// The tile map lists the Ising members' tiles first (ising_tiles of them),
-// then the Potts members' tiles.  Label schedule 0: the Ising tiles in one
-// launch (two-state layout), the Potts tiles in another; schedule 1: every
-// tile in one launch (Potts layout, the member's model picked per tile).
-constexpr int kLabelSchedules = 2;
+// Batched phases: one launch per phase over every tile of every member
+// (Ising/Potts, one dimension, tile shape `shape`), then the step counter
+// advances.  The tile map lists the Ising members' tiles first (ising_tiles
+// of them), then the Potts members' tiles.  A schedule has two bits:
+//   bit 0 (label layout): 0 = the Ising tiles in one launch (two-state
+//     layout), the Potts tiles in another; 1 = every tile in one launch
+//     (Potts layout, the member's model picked per tile);
+//   bit 1 (grid form): 0 = one CTA per tile-map entry; 1 = a persistent grid
+//     of resident CTAs (the SM count times the CTAs one SM holds), each
+//     striding over the tile map.
+constexpr int kBatchSchedules = 4;
 cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ising_tiles,
                                uint32_t potts_tiles, cudaStream_t st);
-cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st);
-cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, uint32_t ntiles, cudaStream_t st);
+cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,
+                               cudaStream_t st);
+cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,
+                              cudaStream_t st);
+
+// Grid of a persistent launch of kernel k with `threads` threads per CTA
+// over n tile-map entries: the device's SM count times the CTAs of k one SM
+// holds (the occupancy calculator's figure, cached per kernel), at most n.
+int sm_count();
+template <class K>
+unsigned batch_grid(K* k, int threads, uint32_t n) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, 0) != cudaSuccess || nb < 1) nb = 1;
+    per_sm = nb;
+  }
+  const uint64_t g = (uint64_t)sm_count() * (uint64_t)per_sm;
+  return (unsigned)(g < n ? g : (n ? n : 1u));
+}
 // Advances the batch step counter (after every member's sweep).
 cudaError_t launch_advance(const BatchView& bv, cudaStream_t st);
 // Small members of a batch (sw_small.cu): one CTA per member, whole sweeps

@@ -336,28 +336,34 @@ constexpr int label_blocks(int threads, int layout) {
   return (layout == 1 ? 5 : 4) * 256 / threads > 32 ? 32 : (layout == 1 ? 5 : 4) * 256 / threads;
 }
 
+// A CTA labels tile-map entries first + t for t = blockIdx.x, blockIdx.x +
+// gridDim.x, ... below first + n: one entry per CTA when the grid covers
+// the map, several when it is a persistent grid of resident CTAs.
 template <class S, int LAYOUT>
 __global__ void __launch_bounds__(S::THREADS, label_blocks(S::THREADS, LAYOUT))
-    k_label_batch(BatchView bv, uint32_t first) {
+    k_label_batch(BatchView bv, uint32_t first, uint32_t n) {
   __shared__ LabelSmem<S, LAYOUT == 1 ? 1 : 2> sm;
   // the member's lattice view is copied to shared memory: the Philox round
   // keys are read on every round
   __shared__ Lattice s_lat;
   static_assert(sizeof(Lattice) % 4 == 0, "lattice copy");
   pdl_wait();
-  const uint32_t b = __ldg(&bv.tile_lattice[first + blockIdx.x]);
-  const uint32_t tile = __ldg(&bv.tile_index[first + blockIdx.x]);
-  const BatchMember& m = bv.members[b];
-  for (uint32_t k = threadIdx.x; k < sizeof(Lattice) / 4; k += S::THREADS)
-    reinterpret_cast<uint32_t*>(&s_lat)[k] = reinterpret_cast<const uint32_t*>(&m.lat)[k];
-  __syncthreads();
   const uint32_t step = *bv.step;
-  if (step >= m.nsweeps) return;  // the member has had its sweeps this call
-  const uint32_t sweep = m.sweep0 + step + 1u;
-  const bool potts = LAYOUT == 2 || (LAYOUT == 3 && s_lat.model == kPotts);
-  if (step == 0u && !m.measure0) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
-  else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
-  else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
+  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+    __syncthreads();  // the previous entry's readers of s_lat and sm are done
+    const uint32_t b = __ldg(&bv.tile_lattice[first + t]);
+    const uint32_t tile = __ldg(&bv.tile_index[first + t]);
+    const BatchMember& m = bv.members[b];
+    for (uint32_t k = threadIdx.x; k < sizeof(Lattice) / 4; k += S::THREADS)
+      reinterpret_cast<uint32_t*>(&s_lat)[k] = reinterpret_cast<const uint32_t*>(&m.lat)[k];
+    __syncthreads();
+    if (step >= m.nsweeps) continue;  // the member has had its sweeps this call
+    const uint32_t sweep = m.sweep0 + step + 1u;
+    const bool potts = LAYOUT == 2 || (LAYOUT == 3 && s_lat.model == kPotts);
+    if (step == 0u && !m.measure0) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
+    else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
+    else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
+  }
 }
 
 // Stand-alone measurement of an Ising (MM 1) or Potts (MM 2) state as the
@@ -678,16 +684,25 @@ cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cud
 
 namespace {
 
+// Schedule bit 0: Ising and Potts tiles in one launch (Potts layout) or
+// two; bit 1: persistent grids (batch_grid).
+template <class S, int LAYOUT>
+cudaError_t label_batch_launch(const BatchView& bv, uint32_t first, uint32_t n, bool persistent,
+                               cudaStream_t st) {
+  const unsigned g = persistent ? batch_grid(k_label_batch<S, LAYOUT>, S::THREADS, n) : n;
+  return launch_pdl(k_label_batch<S, LAYOUT>, g, (unsigned)S::THREADS, st, bv, first, n);
+}
+
 template <int D, int SH>
 cudaError_t label_batch_shape(const BatchView& bv, int schedule, uint32_t ising_tiles, uint32_t potts_tiles,
                               cudaStream_t st) {
   using S = ShapeOf<D, SH>;
-  if (schedule == 1 && ising_tiles && potts_tiles)
-    return launch_pdl(k_label_batch<S, 3>, ising_tiles + potts_tiles, (unsigned)S::THREADS, st, bv, 0u);
+  const bool persistent = (schedule & 2) != 0;
+  if ((schedule & 1) && ising_tiles && potts_tiles)
+    return label_batch_launch<S, 3>(bv, 0u, ising_tiles + potts_tiles, persistent, st);
   cudaError_t e = cudaSuccess;
-  if (ising_tiles) e = launch_pdl(k_label_batch<S, 1>, ising_tiles, (unsigned)S::THREADS, st, bv, 0u);
-  if (e == cudaSuccess && potts_tiles)
-    e = launch_pdl(k_label_batch<S, 2>, potts_tiles, (unsigned)S::THREADS, st, bv, ising_tiles);
+  if (ising_tiles) e = label_batch_launch<S, 1>(bv, 0u, ising_tiles, persistent, st);
+  if (e == cudaSuccess && potts_tiles) e = label_batch_launch<S, 2>(bv, ising_tiles, potts_tiles, persistent, st);
   return e;
 }
 

@@ -50,6 +50,8 @@ _SIGNATURES = {
     "sw_measure": (_i, [_vp, ctypes.POINTER(sw_moments)]),
     "sw_sync": (_i, [_vp]),
     "sw_set_loop_cap": (_i, [_vp, ctypes.c_longlong]),
+    "sw_query": (_i, [_vp]),
+    "sw_batch_query": (_i, [_vp]),
     "sw_set_stream": (_i, [_vp, _vp]),
     "sw_sweep_counter": (_u64, [_vp]),
     "sw_set_sweep_counter": (_i, [_vp, _u64]),
@@ -89,7 +91,7 @@ _SIGNATURES = {
 
 SW_NOALLOC_MAX_SITES = 1 << 21
 SW_LABEL_TILE_UF, SW_LABEL_EQUIVALENCE = 0, 1
-SW_BATCH_TILE_SHAPES, SW_BATCH_LABEL_SCHEDULES = 3, 2
+SW_BATCH_TILE_SHAPES, SW_BATCH_SCHEDULES = 3, 4
 
 
 def library_path() -> str:
@@ -163,6 +165,14 @@ def sw_measure(h: Handle) -> dict:
     m = sw_moments()
     _check(lib().sw_measure(h, ctypes.byref(m)))
     return {f: getattr(m, f) for f, _ in sw_moments._fields_}
+
+
+def sw_query(h: Handle) -> bool:
+    """True once the work enqueued on the handle's stream has completed."""
+    rc = lib().sw_query(h)
+    if rc < 0:
+        _check(rc)
+    return rc == 1
 
 
 def sw_set_loop_cap(h: Handle, cap: int):
@@ -351,6 +361,14 @@ def sw_batch_set_stream(b: Batch, stream: int):
     _check(lib().sw_batch_set_stream(b, ctypes.c_void_p(stream)))
 
 
+def sw_batch_query(b: Batch) -> bool:
+    """True once the batch's enqueued sweeps have completed."""
+    rc = lib().sw_batch_query(b)
+    if rc < 0:
+        _check(rc)
+    return rc == 1
+
+
 def sw_batch_size(b: Batch) -> int:
     return int(lib().sw_batch_size(b))
 
@@ -374,9 +392,9 @@ def sw_batch_get_config(b: Batch) -> dict:
 def sw_batch_autotune(b: Batch, sweeps: int) -> np.ndarray:
     """Times every (shape, schedule) on real sweeps of the batch and keeps the
     fastest; returns ms per sweep as [shape, schedule] (-1 where not tried)."""
-    ms = (ctypes.c_float * (SW_BATCH_TILE_SHAPES * SW_BATCH_LABEL_SCHEDULES))()
+    ms = (ctypes.c_float * (SW_BATCH_TILE_SHAPES * SW_BATCH_SCHEDULES))()
     _check(lib().sw_batch_autotune(b, sweeps, ms))
-    return np.array(list(ms), dtype=np.float64).reshape(SW_BATCH_TILE_SHAPES, SW_BATCH_LABEL_SCHEDULES)
+    return np.array(list(ms), dtype=np.float64).reshape(SW_BATCH_TILE_SHAPES, SW_BATCH_SCHEDULES)
 
 
 def sw_device_bytes(model: int, dim: int, L: int, q: int) -> int:

@@ -63,7 +63,7 @@ def test_clock_parser_keeps_only_the_timed_window():
 
 def test_batch_launch_count():
     """The gpu_launches claim of the batch lines: labels (one per model under
-    schedule 0, one under schedule 1), merge, compression, apply, one small
+    label layout 0, one under layout 1), merge, compression, apply, one small
     kernel per model with one-CTA members, the step counter."""
     import bench
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -73,6 +73,9 @@ def test_batch_launch_count():
     small = [(ising, 2, 32, 2, 2.0, 3), (potts, 2, 90, 4, 0.9, 4), (ising, 2, 80, 2, 2.0, 5)]
     assert bench.batch_launches(big, 0) == 2 + 3 + 1
     assert bench.batch_launches(big, 1) == 1 + 3 + 1
+    # the grid form (bit 1) launches the same kernels
+    assert bench.batch_launches(big, 2) == 2 + 3 + 1
+    assert bench.batch_launches(big, 3) == 1 + 3 + 1
     # Ising L = 80 (6400 sites) is tiled, Potts L = 90 (8100) and Ising L = 32 are one-CTA
     assert bench.batch_launches(small, 0) == 1 + 3 + 2 + 1
     assert bench.batch_launches([(ising, 3, 10, 2, 4.5, 6)], 0) == 0 + 0 + 1 + 1

@@ -1,8 +1,8 @@
 """The serving loop's host logic on CPU, against a fake of the C ABI that
 counts sweeps the way the library does (a batch call advances each member by
 min(n, target - counter)): every job gets exactly its sweeps, XY jobs run
-alone, admission follows arrival order and never exceeds the HBM budget
-(except for a single job larger than the budget, admitted alone)."""
+alone, admission follows arrival order and never exceeds the HBM budget,
+and a job larger than the whole budget is rejected with an error."""
 from __future__ import annotations
 
 import os
@@ -78,6 +78,12 @@ class FakeSw:
     def sw_sync(self, h):
         pass
 
+    def sw_query(self, h):
+        return True                      # the fake's work completes at once
+
+    def sw_batch_query(self, b):
+        return True
+
     def sw_measure(self, h):
         return {"n_sweeps": h.counter}
 
@@ -100,7 +106,7 @@ def test_every_job_gets_its_sweeps_within_the_budget(serve, monkeypatch):
     fake = FakeSw(budget)
     monkeypatch.setattr(serve, "sw", fake)
     s = serve.Server(budget, chunk=64)
-    batches = dict(s.batches)
+    batches = {d: s.groups[d].batch for d in (2, 3)}
     done = s.run(jobs(serve, specs), realtime=False)
     s.close()
     assert sorted(j.id for j in done) == list(range(len(specs)))
@@ -113,14 +119,38 @@ def test_every_job_gets_its_sweeps_within_the_budget(serve, monkeypatch):
     assert all(b.calls and all(n == 64 for n in b.calls) for b in batches.values())
 
 
-def test_a_job_larger_than_the_budget_runs_alone(serve, monkeypatch):
+def test_a_job_larger_than_the_budget_is_rejected(serve, monkeypatch):
     fake = FakeSw(100)
     monkeypatch.setattr(serve, "sw", fake)
-    s = serve.Server(100, chunk=16)
-    done = s.run(jobs(serve, [(0, 2, 64, 40), (1, 2, 8, 3)]), realtime=False)
+    s = serve.Server(10 * 8 ** 2 * 2, chunk=16)
+    done = s.run(jobs(serve, [(0, 2, 64, 40), (1, 2, 8, 3), (2, 3, 4, 5)]), realtime=False)
     s.close()
-    assert [j.result["n_sweeps"] for j in sorted(done, key=lambda j: j.id)] == [40, 3]
-    assert fake.peak_bytes == 10 * 64 ** 2                 # never beside another job
+    assert [j.id for j in done] == [1, 2]
+    assert [j.result["n_sweeps"] for j in done] == [3, 5]
+    assert [j.id for j in s.rejected] == [0] and "budget" in s.rejected[0].error
+    assert fake.peak_bytes <= 10 * 8 ** 2 * 2                # never above the budget
+
+
+def test_groups_advance_independently(serve, monkeypatch):
+    """A group whose chunk is still running is skipped, not waited for: the
+    other groups keep getting chunks meanwhile."""
+    fake = FakeSw(1 << 30)
+    monkeypatch.setattr(serve, "sw", fake)
+    slow = {"busy_polls": 0}
+
+    def batch_query(b):
+        if b.dim == 3 and slow["busy_polls"] < 5:       # the 3D batch lags behind
+            slow["busy_polls"] += 1
+            return False
+        return True
+    fake.sw_batch_query = batch_query
+    s = serve.Server(1 << 30, chunk=8, poll_s=0.0)
+    b2, b3 = s.groups[2].batch, s.groups[3].batch
+    done = s.run(jobs(serve, [(0, 2, 16, 64), (0, 3, 8, 16)]), realtime=False)
+    s.close()
+    assert sorted(j.result["n_sweeps"] for j in done) == [16, 64]
+    # the 2D batch got chunks while the 3D batch's first chunk was still running
+    assert len(b2.calls) == 8 and len(b3.calls) == 2
 
 
 def test_summary_percentiles(serve):
