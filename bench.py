@@ -460,6 +460,9 @@ def run_gpu(args):
         # the ragged batch and the served stream of the same build, one GPU
         legs["batch"] = batch_leg(args, torch.cuda.Stream())   # graph capture needs a non-default stream
         legs["serve"] = serve_leg(args)
+        # the same recipe with smaller jobs (2D L <= 1024, 3D L <= 128, <= 1000
+        # sweeps), where most of the work is latency-bound small lattices
+        legs["serve_small_jobs"] = serve_leg(args, 1024, 128, 1000)
 
     if rank == 0:
         peak, peak_kind = peaks()
@@ -638,13 +641,16 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def serve_leg(args):
+def serve_leg(args, max_l2=None, max_l3=None, max_sweeps=None):
     """Served request stream (seed 1004): continuous batching vs the
     one-at-a-time plain path, at saturation (all queued at t = 0) and at
     0.7 of the serial capacity (Poisson arrivals)."""
     import inputs
     from paper_1403_7560_gb300 import serve
-    kw = dict(max_L2=args.max_l2, max_L3=args.max_l3, sweeps=(100, args.max_sweeps))
+    max_l2 = max_l2 or args.max_l2
+    max_l3 = max_l3 or args.max_l3
+    max_sweeps = max_sweeps or args.max_sweeps
+    kw = dict(max_L2=max_l2, max_L3=max_l3, sweeps=(100, max_sweeps))
     budget = int(args.budget_gb * (1 << 30))
 
     def served(jobs, realtime):
@@ -673,8 +679,8 @@ def serve_leg(args):
             "steps": args.jobs,
             "config": {"workload": f"served stream, seed 1004, {args.jobs} jobs, class uniform over "
                                    "2D Ising / 3D Ising / 2D Potts q=3,4,8 / 3D XY, L log-uniform in "
-                                   f"[16,{args.max_l2}] (2D) or [16,{args.max_l3}] (3D), T = Tc(1+U(-0.02,0.02)), "
-                                   f"sweeps log-uniform in [100,{args.max_sweeps}]",
+                                   f"[16,{max_l2}] (2D) or [16,{max_l3}] (3D), T = Tc(1+U(-0.02,0.02)), "
+                                   f"sweeps log-uniform in [100,{max_sweeps}]",
                        "budget_gb": args.budget_gb, "chunk": args.chunk},
             "saturation": {"served": sat_srv, "serial": sat_ser,
                            "speedup": sat_srv["jobs_per_s"] / sat_ser["jobs_per_s"]},

@@ -127,20 +127,29 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, merge_blocks(Tile<D>::THREAD
   merge_tile<Tile<D>>(lat, blockIdx.x, sm);
 }
 
-// Batch kernels take tile-map entries t = blockIdx.x, blockIdx.x +
-// gridDim.x, ... below n: one per CTA when the grid covers the map, several
-// when it is a persistent grid of resident CTAs.
-template <class S>
-__global__ void __launch_bounds__(S::THREADS, merge_blocks(S::THREADS)) k_merge_batch(BatchView bv, uint32_t n) {
+// Batch kernels: PERSISTENT false launches one CTA per tile-map entry
+// (entry blockIdx.x); PERSISTENT true a grid of resident CTAs, each taking
+// entries t = blockIdx.x, blockIdx.x + gridDim.x, ... below n.  Separate
+// instantiations, so that the loop costs the one-entry kernels no registers.
+template <class S, bool PERSISTENT>
+__global__ void __launch_bounds__(S::THREADS, PERSISTENT ? (merge_blocks(S::THREADS) * 3) / 4 : merge_blocks(S::THREADS))
+    k_merge_batch(BatchView bv, uint32_t n) {
   __shared__ MergeSmem<S> sm;
   pdl_wait();
   const uint32_t step = *bv.step;
-  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
-    __syncthreads();  // the previous entry's readers of sm are done
+  auto entry = [&](uint32_t t) {
     const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
-    if (step >= m.nsweeps) continue;  // the member has had its sweeps this call
+    if (step >= m.nsweeps) return;  // the member has had its sweeps this call
     const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
     merge_tile<S>(lat, __ldg(&bv.tile_index[t]), sm);
+  };
+  if constexpr (PERSISTENT) {
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+      __syncthreads();  // the previous entry's readers of sm are done
+      entry(t);
+    }
+  } else {
+    entry(blockIdx.x);
   }
 }
 
@@ -186,19 +195,25 @@ __global__ void __launch_bounds__(kFlipThreads, 8) k_compress(Lattice lat, Measu
 
 // Batch: one CTA per member tile; the CTA of each member's tile 0 first
 // writes that member's previous record (every step after the first).
-__global__ void __launch_bounds__(kFlipThreads, 6) k_compress_batch(BatchView bv, uint32_t n) {
+template <bool PERSISTENT>
+__global__ void __launch_bounds__(kFlipThreads, PERSISTENT ? 4 : 6) k_compress_batch(BatchView bv, uint32_t n) {
   __shared__ long long s_red[kFlipWarps];
   __shared__ double s_rd[kFlipWarps];
   pdl_wait();
   const uint32_t step = *bv.step;
-  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+  auto entry = [&](uint32_t t) {
     const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
     const uint32_t tile = __ldg(&bv.tile_index[t]);
-    if (step >= m.nsweeps) continue;
+    if (step >= m.nsweeps) return;
     const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
     if (tile == 0u && (step > 0u || m.measure0))
       finalize_record<kFlipWarps>(lat, m.meas, m.sweep0 + step, s_red, s_rd);
     compress_tile(lat, tile);
+  };
+  if constexpr (PERSISTENT) {
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) entry(t);
+  } else {
+    entry(blockIdx.x);
   }
 }
 
@@ -280,15 +295,21 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
 template <class S>
 __device__ __forceinline__ void apply_tile(const BatchMember& m, uint32_t tile, uint32_t step, long long* s_red);
 
-template <class S>
+template <class S, bool PERSISTENT>
 __global__ void __launch_bounds__(kFlipThreads) k_apply_batch(BatchView bv, uint32_t n) {
   __shared__ long long s_red[kFlipThreads / 32];
   pdl_wait();
   const uint32_t step = *bv.step;
-  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
-    const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
-    if (step >= m.nsweeps) continue;
-    apply_tile<S>(m, __ldg(&bv.tile_index[t]), step, s_red);
+  if constexpr (PERSISTENT) {
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+      const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
+      if (step >= m.nsweeps) continue;
+      apply_tile<S>(m, __ldg(&bv.tile_index[t]), step, s_red);
+    }
+  } else {
+    const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[blockIdx.x])];
+    if (step >= m.nsweeps) return;
+    apply_tile<S>(m, __ldg(&bv.tile_index[blockIdx.x]), step, s_red);
   }
 }
 
@@ -411,16 +432,24 @@ namespace {
 template <int D, int SH>
 cudaError_t merge_batch_shape(const BatchView& bv, uint32_t ntiles, bool persistent, cudaStream_t st) {
   using S = ShapeOf<D, SH>;
-  const unsigned g = persistent ? batch_grid(k_merge_batch<S>, S::THREADS, ntiles) : ntiles;
-  return launch_pdl(k_merge_batch<S>, g, (unsigned)S::THREADS, st, bv, ntiles);
+  if (!persistent) return launch_pdl(k_merge_batch<S, false>, ntiles, (unsigned)S::THREADS, st, bv, ntiles);
+  const unsigned g = batch_grid(k_merge_batch<S, true>, S::THREADS, ntiles);
+  return launch_pdl(k_merge_batch<S, true>, g, (unsigned)S::THREADS, st, bv, ntiles);
 }
 
 template <int D, int SH>
 cudaError_t flip_batch_shape(const BatchView& bv, uint32_t ntiles, bool persistent, cudaStream_t st) {
-  const unsigned gc = persistent ? batch_grid(k_compress_batch, kFlipThreads, ntiles) : ntiles;
-  const unsigned ga = persistent ? batch_grid(k_apply_batch<ShapeOf<D, SH>>, kFlipThreads, ntiles) : ntiles;
-  cudaError_t e = launch_pdl(k_compress_batch, gc, kFlipThreads, st, bv, ntiles);
-  if (e == cudaSuccess) e = launch_pdl(k_apply_batch<ShapeOf<D, SH>>, ga, kFlipThreads, st, bv, ntiles);
+  using S = ShapeOf<D, SH>;
+  cudaError_t e;
+  if (!persistent) {
+    e = launch_pdl(k_compress_batch<false>, ntiles, kFlipThreads, st, bv, ntiles);
+    if (e == cudaSuccess) e = launch_pdl(k_apply_batch<S, false>, ntiles, kFlipThreads, st, bv, ntiles);
+    return e;
+  }
+  const unsigned gc = batch_grid(k_compress_batch<true>, kFlipThreads, ntiles);
+  const unsigned ga = batch_grid(k_apply_batch<S, true>, kFlipThreads, ntiles);
+  e = launch_pdl(k_compress_batch<true>, gc, kFlipThreads, st, bv, ntiles);
+  if (e == cudaSuccess) e = launch_pdl(k_apply_batch<S, true>, ga, kFlipThreads, st, bv, ntiles);
   return e;
 }
 

@@ -214,15 +214,15 @@ cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, int sched
 
 // Grid of a persistent launch of kernel k with `threads` threads per CTA
 // over n tile-map entries: the device's SM count times the CTAs of k one SM
-// holds (the occupancy calculator's figure, cached per kernel), at most n.
+// holds (the occupancy calculator's figure for that kernel), at most n.
+// Queried when the batch's graph is captured, not per sweep.
 int sm_count();
 template <class K>
 unsigned batch_grid(K* k, int threads, uint32_t n) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, 0) != cudaSuccess || nb < 1) nb = 1;
-    per_sm = nb;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
   }
   const uint64_t g = (uint64_t)sm_count() * (uint64_t)per_sm;
   return (unsigned)(g < n ? g : (n ? n : 1u));

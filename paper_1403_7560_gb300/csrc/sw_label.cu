@@ -336,33 +336,49 @@ constexpr int label_blocks(int threads, int layout) {
   return (layout == 1 ? 5 : 4) * 256 / threads > 32 ? 32 : (layout == 1 ? 5 : 4) * 256 / threads;
 }
 
-// A CTA labels tile-map entries first + t for t = blockIdx.x, blockIdx.x +
-// gridDim.x, ... below first + n: one entry per CTA when the grid covers
-// the map, several when it is a persistent grid of resident CTAs.
-template <class S, int LAYOUT>
-__global__ void __launch_bounds__(S::THREADS, label_blocks(S::THREADS, LAYOUT))
+// One tile-map entry of a batch label launch: the member's lattice view is
+// copied to shared memory (the Philox round keys are read on every round).
+template <class S, int LAYOUT, class Smem>
+__device__ __forceinline__ void label_batch_entry(const BatchView& bv, uint32_t e, uint32_t step, Smem& sm,
+                                                  Lattice& s_lat) {
+  static_assert(sizeof(Lattice) % 4 == 0, "lattice copy");
+  const uint32_t b = __ldg(&bv.tile_lattice[e]);
+  const uint32_t tile = __ldg(&bv.tile_index[e]);
+  const BatchMember& m = bv.members[b];
+  for (uint32_t k = threadIdx.x; k < sizeof(Lattice) / 4; k += S::THREADS)
+    reinterpret_cast<uint32_t*>(&s_lat)[k] = reinterpret_cast<const uint32_t*>(&m.lat)[k];
+  __syncthreads();
+  if (step >= m.nsweeps) return;  // the member has had its sweeps this call
+  const uint32_t sweep = m.sweep0 + step + 1u;
+  const bool potts = LAYOUT == 2 || (LAYOUT == 3 && s_lat.model == kPotts);
+  if (step == 0u && !m.measure0) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
+  else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
+  else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
+}
+
+// PERSISTENT false: CTA k labels tile-map entry first + k (the grid covers
+// the map).  PERSISTENT true: a grid of resident CTAs, each taking entries
+// first + t for t = blockIdx.x, blockIdx.x + gridDim.x, ... below first + n.
+// Separate instantiations, so that the loop costs the one-entry kernel no
+// registers; the persistent one allows a quarter fewer CTAs per SM (its
+// grid is sized by the occupancy it gets), so that its loop does not spill.
+constexpr int persistent_blocks(int blocks) { return blocks * 3 / 4 > 1 ? blocks * 3 / 4 : 1; }
+
+template <class S, int LAYOUT, bool PERSISTENT>
+__global__ void __launch_bounds__(S::THREADS, PERSISTENT ? persistent_blocks(label_blocks(S::THREADS, LAYOUT))
+                                                         : label_blocks(S::THREADS, LAYOUT))
     k_label_batch(BatchView bv, uint32_t first, uint32_t n) {
   __shared__ LabelSmem<S, LAYOUT == 1 ? 1 : 2> sm;
-  // the member's lattice view is copied to shared memory: the Philox round
-  // keys are read on every round
   __shared__ Lattice s_lat;
-  static_assert(sizeof(Lattice) % 4 == 0, "lattice copy");
   pdl_wait();
   const uint32_t step = *bv.step;
-  for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
-    __syncthreads();  // the previous entry's readers of s_lat and sm are done
-    const uint32_t b = __ldg(&bv.tile_lattice[first + t]);
-    const uint32_t tile = __ldg(&bv.tile_index[first + t]);
-    const BatchMember& m = bv.members[b];
-    for (uint32_t k = threadIdx.x; k < sizeof(Lattice) / 4; k += S::THREADS)
-      reinterpret_cast<uint32_t*>(&s_lat)[k] = reinterpret_cast<const uint32_t*>(&m.lat)[k];
-    __syncthreads();
-    if (step >= m.nsweeps) continue;  // the member has had its sweeps this call
-    const uint32_t sweep = m.sweep0 + step + 1u;
-    const bool potts = LAYOUT == 2 || (LAYOUT == 3 && s_lat.model == kPotts);
-    if (step == 0u && !m.measure0) label_tile<S, false, 0>(s_lat, tile, sweep, m.meas, sm);
-    else if (LAYOUT != 1 && potts) label_tile<S, false, 2>(s_lat, tile, sweep, m.meas, sm);
-    else if (LAYOUT != 2) label_tile<S, false, 1>(s_lat, tile, sweep, m.meas, sm);
+  if constexpr (PERSISTENT) {
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
+      __syncthreads();  // the previous entry's readers of s_lat and sm are done
+      label_batch_entry<S, LAYOUT>(bv, first + t, step, sm, s_lat);
+    }
+  } else {
+    label_batch_entry<S, LAYOUT>(bv, first + blockIdx.x, step, sm, s_lat);
   }
 }
 
@@ -689,8 +705,9 @@ namespace {
 template <class S, int LAYOUT>
 cudaError_t label_batch_launch(const BatchView& bv, uint32_t first, uint32_t n, bool persistent,
                                cudaStream_t st) {
-  const unsigned g = persistent ? batch_grid(k_label_batch<S, LAYOUT>, S::THREADS, n) : n;
-  return launch_pdl(k_label_batch<S, LAYOUT>, g, (unsigned)S::THREADS, st, bv, first, n);
+  if (!persistent) return launch_pdl(k_label_batch<S, LAYOUT, false>, n, (unsigned)S::THREADS, st, bv, first, n);
+  const unsigned g = batch_grid(k_label_batch<S, LAYOUT, true>, S::THREADS, n);
+  return launch_pdl(k_label_batch<S, LAYOUT, true>, g, (unsigned)S::THREADS, st, bv, first, n);
 }
 
 template <int D, int SH>
