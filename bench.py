@@ -511,7 +511,7 @@ def _job_list(specs):
 def batch_launches(specs, schedule):
     """Kernels one batch sweep launches: the tiled members' labels (one
     launch per model under label layout 0, one in all under layout 1 -- bit 0
-    of the schedule), merge,
+    of the schedule), merge (one launch, or one per axis under bit 2),
     compression and apply; one launch per model of the small members (2D
     Ising up to 4096 sites, 2D Potts up to 8192, 3D up to 1024); the step
     counter."""
@@ -520,7 +520,9 @@ def batch_launches(specs, schedule):
     tiled = {m for (m, d, L, _, _, _) in specs if not is_small(m, d, L)}
     small = {m for (m, d, L, _, _, _) in specs if is_small(m, d, L)}
     labels = (len(tiled) if (schedule & 1) == 0 else 1) if tiled else 0
-    return labels + (3 if tiled else 0) + len(small) + 1
+    dim = specs[0][1] if specs else 2
+    merges = (dim if schedule & 4 else 1) if tiled else 0
+    return labels + (merges + 2 if tiled else 0) + len(small) + 1
 
 
 def small_batch(sw, inputs, st, sweeps=50):

@@ -311,9 +311,11 @@ size_t sw_series_capacity(void);
  * tiles in another, 1 runs all tiles in one launch with the Potts layout.
  * Bit 1 is the grid form of every phase (labels, merge, compression, apply):
  * 0 launches one CTA per tile, 1 launches a persistent grid -- the SM count
- * times the CTAs one SM holds -- whose CTAs stride over the tile map.  No
+ * times the CTAs one SM holds -- whose CTAs stride over the tile map.  Bit 2
+ * is the merge schedule: 0 joins every face of every tile in one launch, 1
+ * in one launch per axis (the x faces of all tiles, then y, then z).  No
  * configuration changes any result: bonds, draws and canonical labels are
- * keyed by row word and site index, not by tile or CTA.
+ * keyed by row word and site index, not by tile, CTA or union order.
  * sw_batch_set_config(b, shape, schedule)   selects one (SW_ERR_BAD_ARG out
  *                          of range); the next sweep recaptures the graph.
  * sw_batch_get_config(b, &shape, &schedule, &tile_y, &tile_z)   the current
@@ -324,19 +326,19 @@ size_t sw_series_capacity(void);
  *                          upload), then `sweeps` sweeps timed with CUDA
  *                          events (a host wait).  These are real measured
  *                          sweeps of every member, as sw_batch_sweep's: with
- *                          C = 3 shapes x 2 grid forms x (2 label layouts
- *                          if the batch holds both Ising and Potts lattices,
- *                          else 1), every counter advances by
- *                          C * (sweeps + 1).  ms (NULL or
+ *                          C = 3 shapes x 2 grid forms x 2 merge schedules
+ *                          x (2 label layouts if the batch holds both Ising
+ *                          and Potts lattices, else 1), every counter
+ *                          advances by C * (sweeps + 1).  ms (NULL or
  *                          SW_BATCH_TILE_SHAPES * SW_BATCH_SCHEDULES floats,
- *                          index shape * 4 + schedule) receives the
+ *                          index shape * 8 + schedule) receives the
  *                          time per sweep of each configuration, -1 where not
  *                          tried.  An empty batch returns SW_OK untouched;
  *                          sweeps < 1, or a member whose sweep target lies
  *                          within the C * (sweeps + 1) sweeps, is
  *                          SW_ERR_BAD_ARG. */
 #define SW_BATCH_TILE_SHAPES 3
-#define SW_BATCH_SCHEDULES 4
+#define SW_BATCH_SCHEDULES 8
 typedef struct sw_batch sw_batch;
 sw_batch* sw_batch_create(int dim);
 void sw_batch_destroy(sw_batch* b);

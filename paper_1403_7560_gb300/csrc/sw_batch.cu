@@ -429,9 +429,10 @@ int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep) {
   bool ising = false, potts = false;
   for (const sw_handle* h : b->members) (h->model == SW_POTTS ? potts : ising) = true;
   // one label launch differs from two only when both kinds are present
-  // (schedule bit 0); both grid forms are always tried (bit 1)
+  // (schedule bit 0); both grid forms (bit 1) and merge forms (bit 2) are
+  // always tried
   const bool both = ising && potts;
-  const uint64_t total = (uint64_t)swgb::kTileShapes * (both ? 4 : 2) * ((uint64_t)sweeps + 1);
+  const uint64_t total = (uint64_t)swgb::kTileShapes * (both ? 8 : 4) * ((uint64_t)sweeps + 1);
   for (const sw_handle* h : b->members) {
     if (h->sweep + total >= 0xffffffffull) return bfail(SW_ERR_BAD_ARG, "sweep counter exhausted");
     // every configuration must time the same members

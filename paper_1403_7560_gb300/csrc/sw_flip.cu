@@ -40,8 +40,12 @@ struct MergeSmem {
   int n;
 };
 
+// faces: which of the tile's +x (1), +y (2), +z (4) faces to join; a merge
+// split into one launch per axis starts the tile's hooked list with the x
+// faces and appends to it in the later launches.
 template <class S>
-__device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, MergeSmem<S>& sm) {
+__device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, MergeSmem<S>& sm,
+                                           uint32_t faces = 7u) {
   constexpr int D = S::D, TY = S::TY, TZ = S::TZ, NT = S::THREADS;
   constexpr int NC = MergeShape<S>::kPerThread;
   uint2* s_list = sm.list;
@@ -50,9 +54,9 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   const int L = lat.L;
   const int shift = lat.sbits + 1;
   const int nx = min(32, L - tc.x0), ny = min(TY, L - tc.y0), nz = (D == 3) ? min(TZ, L - tc.z0) : 1;
-  const int cx = (lat.ntx > 1) ? ny * nz : 0;
-  const int cy = (lat.nty > 1) ? nx * nz : 0;
-  const int cz = (D == 3 && lat.ntz > 1) ? nx * ny : 0;
+  const int cx = (lat.ntx > 1 && (faces & 1u)) ? ny * nz : 0;
+  const int cy = (lat.nty > 1 && (faces & 2u)) ? nx * nz : 0;
+  const int cz = (D == 3 && lat.ntz > 1 && (faces & 4u)) ? nx * ny : 0;
   const int total = cx + cy + cz;
   const uint32_t plane = lat.R * (uint32_t)lat.W;
   const int lane = threadIdx.x & 31;
@@ -104,12 +108,12 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
   }
   __syncthreads();
   const int n = s_n;
-  __syncthreads();
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
   // every root this tile hooks goes to the tile's hooked list for k_compress
   // (no list on the labeling-only paths)
   uint32_t* hooked = lat.hooked ? lat.hooked + (size_t)tile * (size_t)lat.hook_cap : nullptr;
+  __syncthreads();
+  if (threadIdx.x == 0) s_n = (hooked && !(faces & 1u)) ? (int)__ldcg(&lat.nhooked[tile]) : 0;
+  __syncthreads();
   for (int e = threadIdx.x; e < n; e += NT) {
     const uint32_t h = gunion(lat.forest, s_list[e].x, s_list[e].y, lat.sbits, lat.err, lat.cap);
     if (hooked && h != 0xffffffffu) hooked[atomicAdd(&s_n, 1)] = h;
@@ -122,9 +126,10 @@ __device__ __forceinline__ void merge_tile(const Lattice& lat, uint32_t tile, Me
 constexpr int merge_blocks(int threads) { return 8 * 256 / threads > 32 ? 32 : 8 * 256 / threads; }
 
 template <int D>
-__global__ void __launch_bounds__(Tile<D>::THREADS, merge_blocks(Tile<D>::THREADS)) k_merge(Lattice lat) {
+__global__ void __launch_bounds__(Tile<D>::THREADS, merge_blocks(Tile<D>::THREADS))
+    k_merge(Lattice lat, uint32_t faces) {
   __shared__ MergeSmem<Tile<D>> sm;
-  merge_tile<Tile<D>>(lat, blockIdx.x, sm);
+  merge_tile<Tile<D>>(lat, blockIdx.x, sm, faces);
 }
 
 // Batch kernels: PERSISTENT false launches one CTA per tile-map entry
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, merge_blocks(Tile<D>::THREAD
 // instantiations, so that the loop costs the one-entry kernels no registers.
 template <class S, bool PERSISTENT>
 __global__ void __launch_bounds__(S::THREADS, PERSISTENT ? (merge_blocks(S::THREADS) * 3) / 4 : merge_blocks(S::THREADS))
-    k_merge_batch(BatchView bv, uint32_t n) {
+    k_merge_batch(BatchView bv, uint32_t n, uint32_t faces) {
   __shared__ MergeSmem<S> sm;
   pdl_wait();
   const uint32_t step = *bv.step;
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(S::THREADS, PERSISTENT ? (merge_blocks(S::THRE
     const BatchMember& m = bv.members[__ldg(&bv.tile_lattice[t])];
     if (step >= m.nsweeps) return;  // the member has had its sweeps this call
     const Lattice lat = m.lat;  // a private copy: global stores cannot alias it
-    merge_tile<S>(lat, __ldg(&bv.tile_index[t]), sm);
+    merge_tile<S>(lat, __ldg(&bv.tile_index[t]), sm, faces);
   };
   if constexpr (PERSISTENT) {
     for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) {
@@ -409,8 +414,8 @@ void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words)
 
 cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
   const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  if (lat.dim == 2) return launch_pdl(k_merge<2>, g, (unsigned)Tile<2>::THREADS, st, lat);
-  return launch_pdl(k_merge<3>, g, (unsigned)Tile<3>::THREADS, st, lat);
+  if (lat.dim == 2) return launch_pdl(k_merge<2>, g, (unsigned)Tile<2>::THREADS, st, lat, 7u);
+  return launch_pdl(k_merge<3>, g, (unsigned)Tile<3>::THREADS, st, lat, 7u);
 }
 
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
@@ -429,12 +434,20 @@ cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Mea
 
 namespace {
 
+// One merge launch over every tile's faces, or (split) one launch per axis:
+// the x faces of every tile, then the y faces, then the z faces.
 template <int D, int SH>
-cudaError_t merge_batch_shape(const BatchView& bv, uint32_t ntiles, bool persistent, cudaStream_t st) {
+cudaError_t merge_batch_shape(const BatchView& bv, uint32_t ntiles, bool persistent, bool split, cudaStream_t st) {
   using S = ShapeOf<D, SH>;
-  if (!persistent) return launch_pdl(k_merge_batch<S, false>, ntiles, (unsigned)S::THREADS, st, bv, ntiles);
-  const unsigned g = batch_grid(k_merge_batch<S, true>, S::THREADS, ntiles);
-  return launch_pdl(k_merge_batch<S, true>, g, (unsigned)S::THREADS, st, bv, ntiles);
+  const unsigned g = persistent ? batch_grid(k_merge_batch<S, true>, S::THREADS, ntiles) : ntiles;
+  auto one = [&](uint32_t faces) {
+    return persistent ? launch_pdl(k_merge_batch<S, true>, g, (unsigned)S::THREADS, st, bv, ntiles, faces)
+                      : launch_pdl(k_merge_batch<S, false>, g, (unsigned)S::THREADS, st, bv, ntiles, faces);
+  };
+  if (!split) return one(7u);
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < D && e == cudaSuccess; ++d) e = one(1u << d);
+  return e;
 }
 
 template <int D, int SH>
@@ -454,10 +467,11 @@ cudaError_t flip_batch_shape(const BatchView& bv, uint32_t ntiles, bool persiste
 }
 
 template <int D>
-cudaError_t merge_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, bool persistent, cudaStream_t st) {
-  if (shape == 1) return merge_batch_shape<D, 1>(bv, ntiles, persistent, st);
-  if (shape == 2) return merge_batch_shape<D, 2>(bv, ntiles, persistent, st);
-  return merge_batch_shape<D, 0>(bv, ntiles, persistent, st);
+cudaError_t merge_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, bool persistent, bool split,
+                            cudaStream_t st) {
+  if (shape == 1) return merge_batch_shape<D, 1>(bv, ntiles, persistent, split, st);
+  if (shape == 2) return merge_batch_shape<D, 2>(bv, ntiles, persistent, split, st);
+  return merge_batch_shape<D, 0>(bv, ntiles, persistent, split, st);
 }
 
 template <int D>
@@ -472,9 +486,9 @@ cudaError_t flip_batch_dim(const BatchView& bv, int shape, uint32_t ntiles, bool
 cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,
                                cudaStream_t st) {
   static_assert(kTileShapes == 3, "one instantiation per shape");
-  const bool persistent = (schedule & 2) != 0;
-  return dim == 2 ? merge_batch_dim<2>(bv, shape, ntiles, persistent, st)
-                  : merge_batch_dim<3>(bv, shape, ntiles, persistent, st);
+  const bool persistent = (schedule & 2) != 0, split = (schedule & 4) != 0;
+  return dim == 2 ? merge_batch_dim<2>(bv, shape, ntiles, persistent, split, st)
+                  : merge_batch_dim<3>(bv, shape, ntiles, persistent, split, st);
 }
 
 cudaError_t launch_flip_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,

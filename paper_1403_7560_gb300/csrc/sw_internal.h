@@ -203,8 +203,10 @@ cudaError_t launch_labels_out(const Lattice& lat, int32_t* out, cudaStream_t st)
 //     (Potts layout, the member's model picked per tile);
 //   bit 1 (grid form): 0 = one CTA per tile-map entry; 1 = a persistent grid
 //     of resident CTAs (the SM count times the CTAs one SM holds), each
-//     striding over the tile map.
-constexpr int kBatchSchedules = 4;
+//     striding over the tile map;
+//   bit 2 (merge): 0 = one launch joins every face of every tile; 1 = one
+//     launch per axis (the x faces of every tile, then y, then z).
+constexpr int kBatchSchedules = 8;
 cudaError_t launch_label_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ising_tiles,
                                uint32_t potts_tiles, cudaStream_t st);
 cudaError_t launch_merge_batch(const BatchView& bv, int dim, int shape, int schedule, uint32_t ntiles,

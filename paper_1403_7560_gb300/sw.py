@@ -91,7 +91,7 @@ _SIGNATURES = {
 
 SW_NOALLOC_MAX_SITES = 1 << 21
 SW_LABEL_TILE_UF, SW_LABEL_EQUIVALENCE = 0, 1
-SW_BATCH_TILE_SHAPES, SW_BATCH_SCHEDULES = 3, 4
+SW_BATCH_TILE_SHAPES, SW_BATCH_SCHEDULES = 3, 8
 
 
 def library_path() -> str:

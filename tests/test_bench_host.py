@@ -73,9 +73,12 @@ def test_batch_launch_count():
     small = [(ising, 2, 32, 2, 2.0, 3), (potts, 2, 90, 4, 0.9, 4), (ising, 2, 80, 2, 2.0, 5)]
     assert bench.batch_launches(big, 0) == 2 + 3 + 1
     assert bench.batch_launches(big, 1) == 1 + 3 + 1
-    # the grid form (bit 1) launches the same kernels
+    # the grid form (bit 1) launches the same kernels; the merge split by
+    # axis (bit 2) launches one merge per axis
     assert bench.batch_launches(big, 2) == 2 + 3 + 1
     assert bench.batch_launches(big, 3) == 1 + 3 + 1
+    assert bench.batch_launches(big, 4) == 2 + 4 + 1
+    assert bench.batch_launches([(ising, 3, 64, 2, 4.5, 7)], 5) == 1 + 5 + 1
     # Ising L = 80 (6400 sites) is tiled, Potts L = 90 (8100) and Ising L = 32 are one-CTA
     assert bench.batch_launches(small, 0) == 1 + 3 + 2 + 1
     assert bench.batch_launches([(ising, 3, 10, 2, 4.5, 6)], 0) == 0 + 0 + 1 + 1

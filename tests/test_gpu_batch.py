@@ -141,12 +141,13 @@ def test_batch_rules(sw):
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2])
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
+@pytest.mark.parametrize("schedule", list(range(8)))
 @pytest.mark.parametrize("specs", [SPECS_2D, SPECS_3D], ids=["2d", "3d"])
 def test_every_launch_configuration_equals_alone(sw, specs, shape, schedule):
-    """Tile shapes, label layouts and grid forms (one CTA per tile or a
-    persistent grid striding over the tile map) change no result: every
-    member is bit-identical to the same lattice advanced alone."""
+    """Tile shapes, label layouts, grid forms (one CTA per tile or a
+    persistent grid striding over the tile map) and merge schedules (one
+    launch, or one per axis) change no result: every member is
+    bit-identical to the same lattice advanced alone."""
     dim = specs[0][1]
     b = sw.sw_batch_create(dim)
     inb = [make(sw, s, 700 + k) for k, s in enumerate(specs)]
@@ -180,8 +181,8 @@ def test_autotune_keeps_the_fastest_and_changes_no_result(sw):
             sw.sw_batch_add(b, h)
         sw.sw_batch_sweep(b, 2)
         ms = sw.sw_batch_autotune(b, 2)
-        # Ising and Potts members: every shape with both label layouts and
-        # both grid forms
+        # Ising and Potts members: every shape with both label layouts, both
+        # grid forms and both merge schedules
         assert ms.shape == (sw.SW_BATCH_TILE_SHAPES, sw.SW_BATCH_SCHEDULES)
         assert np.all(ms > 0)
         cfg = sw.sw_batch_get_config(b)
@@ -191,7 +192,7 @@ def test_autotune_keeps_the_fastest_and_changes_no_result(sw):
             assert sw.sw_sweep_counter(h) == tuned
         sw.sw_batch_sweep(b, 3)
         # a configuration switch between calls, then more sweeps
-        sw.sw_batch_set_config(b, (cfg["shape"] + 1) % 3, 3 - cfg["schedule"])
+        sw.sw_batch_set_config(b, (cfg["shape"] + 1) % 3, 7 - cfg["schedule"])
         sw.sw_batch_sweep(b, 2)
         for h in alone:
             sw.sw_sweep(h, tuned + 5)
@@ -210,15 +211,16 @@ def test_autotune_of_one_model_tries_one_schedule(sw):
         for h in hs:
             sw.sw_batch_add(b, h)
         ms = sw.sw_batch_autotune(b, 1)
-        # one model: the label layouts coincide, both grid forms are timed
-        assert np.all(ms[:, [0, 2]] > 0) and np.all(ms[:, [1, 3]] == -1)
-        assert sw.sw_batch_get_config(b)["schedule"] in (0, 2)
+        # one model: the label layouts coincide; both grid forms and both
+        # merge schedules are timed
+        assert np.all(ms[:, [0, 2, 4, 6]] > 0) and np.all(ms[:, [1, 3, 5, 7]] == -1)
+        assert sw.sw_batch_get_config(b)["schedule"] in (0, 2, 4, 6)
         for h in hs:
-            assert sw.sw_sweep_counter(h) == 3 * 2 * 2
+            assert sw.sw_sweep_counter(h) == 3 * 4 * 2
         with pytest.raises(sw.SwError):
             sw.sw_batch_set_config(b, 3, 0)
         with pytest.raises(sw.SwError):
-            sw.sw_batch_set_config(b, 0, 4)
+            sw.sw_batch_set_config(b, 0, 8)
         with pytest.raises(sw.SwError):
             sw.sw_batch_autotune(b, 0)
     finally:
