@@ -180,9 +180,10 @@ int sw_query(sw_handle* h);
  *              after cap steps (0: at once; used by the tests to exercise
  *              the error path without a fault)
  *   cap < 0    restores the production cap (2^22 steps)
- * Takes effect for launches enqueued after the call; a batch member keeps
- * the cap it had when it joined its batch.  Returns SW_ERR_BAD_ARG for a
- * NULL handle or cap > 2^22. */
+ * Takes effect for launches enqueued after the call; a batch member runs
+ * with the cap its handle had when the batch last captured its sweep (a
+ * member joining or leaving, or a configuration change, recaptures it).
+ * Returns SW_ERR_BAD_ARG for a NULL handle or cap > 2^22. */
 int sw_set_loop_cap(sw_handle* h, long long cap);
 
 /* Use `stream` (a cudaStream_t, e.g. torch.cuda.Stream.cuda_stream; NULL =

@@ -5,9 +5,11 @@ number of measured sweeps; its result is the moments of sw_measure.
 
 The engine keeps a set of independently advancing groups on the GPU: the
 ragged batch of each dimension (its Ising/Potts jobs, one launch per phase
-over all their tiles, sw_batch_*) and every XY job on its own handle and
-stream.  A group gets a chunk of sweeps, and the host polls it without
-blocking (sw_batch_query / sw_query).  As soon as a group's chunk is done
+over all their tiles, sw_batch_*) and every job that runs alone on its own
+handle and stream -- the XY jobs, and lattices of at least `solo_sites`
+sites, which fill the GPU by themselves and run faster on the single-lattice
+path than inside a batch.  A group gets a chunk of sweeps, and the host
+polls it without blocking (sw_batch_query / sw_query).  As soon as a group's chunk is done
 the engine retires its finished jobs (sw_measure, destroy), lets queued jobs
 join it, and enqueues its next chunk -- so a group never waits for another
 group, and requests that arrive while others run are admitted as memory
@@ -73,7 +75,7 @@ class _Active:
 
 class _Group:
     """What the engine advances as one unit: the batch of one dimension or
-    one XY job.  `busy` is set while a chunk is enqueued."""
+    one job running alone.  `busy` is set while a chunk is enqueued."""
     __slots__ = ("key", "batch", "members", "joining", "busy")
 
     def __init__(self, key, batch=None):
@@ -87,9 +89,10 @@ class Server:
     """Continuous-batching engine over the C ABI (one GPU, current device)."""
 
     def __init__(self, budget_bytes: int, chunk: int = 64, max_active: int = 1024,
-                 poll_s: float = 2e-4):
+                 poll_s: float = 2e-4, solo_sites: int = 1 << 22):
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
+        self.solo_sites = int(solo_sites)
         self.max_active = int(max_active)
         self.poll_s = float(poll_s)
         self.used = 0
@@ -134,8 +137,8 @@ class Server:
             self.used += nbytes
             job.start = now
             a = _Active(job, h, nbytes)
-            if job.model == sw.SW_XY:
-                g = _Group(("xy", job.id))
+            if job.model == sw.SW_XY or job.sites >= self.solo_sites:
+                g = _Group(("solo", job.id))
                 self.groups[g.key] = g
             else:
                 sw.sw_set_sweep_target(h, job.sweeps)
@@ -198,7 +201,7 @@ class Server:
                 self._launch(g)
                 advanced = True
             elif g.batch is None:
-                del self.groups[key]               # a finished XY job's group
+                del self.groups[key]               # a finished solo job's group
         return advanced
 
     def run(self, jobs: list[Job], realtime: bool = True) -> list[Job]:
