@@ -403,7 +403,9 @@ int merge_list_capacity(int dim, int shape) {
 void tile_buffers(int model, int dim, int L, size_t* ntiles, size_t* hook_words) {
   const bool batchable = model == kIsing || model == kPotts;
   *ntiles = *hook_words = 0;
-  for (int s = 0; s < (batchable ? kTileShapes : 1); ++s) {
+  // the single-lattice shape (-1) always; every batch shape for the models a
+  // batch can hold
+  for (int s = -1; s < (batchable ? kTileShapes : 0); ++s) {
     int ntx, nty, ntz;
     tiles_for(dim, L, &ntx, &nty, &ntz, s);
     const size_t n = (size_t)ntx * nty * ntz;

@@ -105,6 +105,13 @@ def test_device_bytes_accounting(swlib):
     assert db(swlib.SW_ISING, 2, 64, 2) < db(swlib.SW_ISING, 2, 128, 2) < db(swlib.SW_ISING, 2, 256, 2)
     for bad in ((9, 2, 16, 2), (0, 4, 16, 2), (0, 2, 3, 2), (0, 3, 2000, 2)):
         assert db(*bad) == 0
+    # lattices no batch can hold (XY, clock) still get the tile buffers of the
+    # single-lattice tiles: 2D L = 4096 in 32x128 tiles, 4096 tiles of 160
+    # hooked words (the 32x256 tiles would need only 2048 x 288)
+    n2 = 4096 ** 2
+    for model in (swlib.SW_XY, swlib.SW_CLOCK):
+        spin = 4 if model == swlib.SW_XY else 2
+        assert db(model, 2, 4096, 4) >= spin * n2 + 2 * n2 // 32 + 4 * n2 + 4096 * 160 * 4 + 4096 * 4
 
 
 @pytest.mark.parametrize("dim,L,mask,labels,needle", [
