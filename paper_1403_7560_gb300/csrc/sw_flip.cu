@@ -16,7 +16,8 @@
 //   its own word.
 // k_apply: every site reads its local root's word (or its own) and writes
 //   its new state (set at random for Ising/Potts, reflection about the
-//   mirror line for XY); global roots are counted.
+//   mirror line for XY); global roots are counted.  Ising and Potts states
+//   are bytes: a thread takes four consecutive sites (k_apply_bytes).
 // k_labels_out: canonical labels (walk to the root) for readout.
 #include <algorithm>
 
@@ -222,11 +223,62 @@ __global__ void __launch_bounds__(kFlipThreads, PERSISTENT ? 4 : 6) k_compress_b
   }
 }
 
-// Every site takes its cluster's draw from its own word (local roots, now
-// compressed) or its local root's word, and writes its new state.
+// Ising and Potts: every site takes its cluster's draw from its own word
+// (local roots, now compressed) or its local root's word, and its new state
+// is that draw (Ising: 1 = -1).  A thread takes four consecutive sites per
+// step: one 16-byte load of their forest words, one 4-byte store of their
+// states.  The local-root words are read through L1: each of a warp's four
+// gathers (site j of every lane) spans the warp's 128 sites, so the four
+// reach the same lines, and L1 serves the repeats (the forest is read-only
+// in this kernel).
+// All buffers come from the device pool, so 16- and 4-byte accesses are
+// aligned; the last N mod 4 sites are taken one by one.
+template <int MODEL>
+__global__ void __launch_bounds__(kFlipThreads) k_apply_bytes(Lattice lat, uint32_t sweep, Measure mb,
+                                                              bool count) {
+  __shared__ long long s_red[kFlipWarps];
+  pdl_wait();
+  const int sb = lat.sbits, shift = sb + 1;
+  const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
+  const uint32_t nq = lat.N >> 2;
+  const uint4* f4 = reinterpret_cast<const uint4*>(lat.forest);
+  uint32_t* s4 = static_cast<uint32_t*>(lat.spins);
+  auto state = [](uint32_t draw) -> uint32_t { return MODEL == kIsing ? (draw ? 0xffu : 0x01u) : draw; };
+  long long roots = 0;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const uint4 w4 = __ldcg(&f4[q]);
+    uint32_t v[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!(v[j] & lr_bit)) v[j] = __ldg(&lat.forest[v[j] >> shift]);
+      else if ((v[j] >> shift) == 4u * q + (uint32_t)j) ++roots;  // a cluster's root
+    }
+    uint32_t packed = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) packed |= state(v[j] & dmask) << (8 * j);
+    s4[q] = packed;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (lat.N & 3u)) {
+    const uint32_t i = 4u * nq + threadIdx.x;
+    uint32_t v = __ldcg(&lat.forest[i]);
+    if (!(v & lr_bit)) v = __ldg(&lat.forest[v >> shift]);
+    else if ((v >> shift) == i) ++roots;
+    static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)state(v & dmask);
+  }
+  if (count) {
+    const long long tot = block_combine<kFlipWarps>(warp_sum(roots), s_red);
+    if (threadIdx.x == 0 && tot)
+      atomicAdd(mb.nclusters + kSlots * (sweep & 1u) + (blockIdx.x % kSlots), (unsigned long long)tot);
+  }
+}
+
+// XY and clock: every site takes its cluster's draw from its own word
+// (local roots, now compressed) or its local root's word; a drawn cluster
+// reflects (XY: about the sweep's mirror line; clock: s -> mirror - s).
 template <int MODEL>
 __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sweep, Measure mb,
                                                          bool count) {
+  static_assert(MODEL == kXY || MODEL == kClock, "Ising and Potts take k_apply_bytes");
   __shared__ float s_phi;
   __shared__ uint32_t s_mirror;
   __shared__ long long s_red[kFlipWarps];
@@ -266,11 +318,7 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
       const uint32_t i = base + k * stride;
       if (i >= lat.N) continue;
       const uint32_t draw = v[k] & dmask;
-      if (MODEL == kIsing) {
-        static_cast<int8_t*>(lat.spins)[i] = draw ? (int8_t)-1 : (int8_t)1;
-      } else if (MODEL == kPotts) {
-        static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)draw;
-      } else if (MODEL == kClock) {
+      if (MODEL == kClock) {
         if (draw) {
           uint16_t* sp = static_cast<uint16_t*>(lat.spins);
           const int q = lat.q;
@@ -422,14 +470,18 @@ cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
 
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
                         uint32_t finalize, cudaStream_t st) {
-  unsigned g = (lat.N + kFlipThreads * kFlipUnroll - 1) / (kFlipThreads * kFlipUnroll);
+  // byte states: a thread per four sites; XY and clock: kFlipUnroll sites
+  // in flight per thread; at most kFlipBlocks CTAs striding over the sites
+  const bool bytes = model == kIsing || model == kPotts;
+  const uint32_t per_block = bytes ? 4u * kFlipThreads : (uint32_t)(kFlipThreads * kFlipUnroll);
+  unsigned g = (unsigned)((lat.N + per_block - 1) / per_block);
   if (g > kFlipBlocks) g = kFlipBlocks;
   if (g == 0) g = 1;
   const unsigned ntiles = (unsigned)(lat.ntx * lat.nty * lat.ntz);
   const cudaError_t e = launch_pdl(k_compress, ntiles, kFlipThreads, st, lat, m, finalize);
   if (e != cudaSuccess) return e;
-  if (model == kIsing) return launch_pdl(k_apply<kIsing>, g, kFlipThreads, st, lat, sweep, m, count);
-  if (model == kPotts) return launch_pdl(k_apply<kPotts>, g, kFlipThreads, st, lat, sweep, m, count);
+  if (model == kIsing) return launch_pdl(k_apply_bytes<kIsing>, g, kFlipThreads, st, lat, sweep, m, count);
+  if (model == kPotts) return launch_pdl(k_apply_bytes<kPotts>, g, kFlipThreads, st, lat, sweep, m, count);
   if (model == kClock) return launch_pdl(k_apply<kClock>, g, kFlipThreads, st, lat, sweep, m, count);
   return launch_pdl(k_apply<kXY>, g, kFlipThreads, st, lat, sweep, m, count);
 }
