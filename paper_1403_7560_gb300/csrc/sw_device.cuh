@@ -204,16 +204,27 @@ __device__ __forceinline__ void sunion(uint32_t* par, uint32_t a, uint32_t b, in
 // The roots of a and b, the two walks advanced in lockstep so that their
 // loads are in flight together; each step on a non-root halves its path
 // (the word of the node walked from is pointed at its grandparent).
+// The walks read through L1 (ld.global.ca): the walks of one CTA meet on
+// the same upper nodes.  L1 is not coherent with the other SMs' stores, so
+// a word read may be older than L2's, but every word ever stored points to
+// a smaller index of the same tree: an old word sends a walk along a longer
+// path to an ancestor, or ends it at a node that has since been hooked, and
+// gunion's atomicMin (in L2) then returns the node's real parent and the
+// union continues from there.  Path halving with an old grandparent still
+// stores an ancestor.  Only the atomic decides that a root is hooked.
+// Earlier kernels' stores are not an issue: every caller reads the forest
+// after griddepcontrol.wait (or a kernel boundary), which makes them
+// visible to the grid's loads.
 __device__ __forceinline__ void gfind2(uint32_t* f, uint32_t& a, uint32_t& b, int shift, uint32_t marker) {
   bool da = false, db = false;
   for (int it = 0; it < (1 << 22); ++it) {
-    const uint32_t pa = da ? a : __ldcg(&f[a]) >> shift;
-    const uint32_t pb = db ? b : __ldcg(&f[b]) >> shift;
+    const uint32_t pa = da ? a : __ldca(&f[a]) >> shift;
+    const uint32_t pb = db ? b : __ldca(&f[b]) >> shift;
     da = da || pa == a;
     db = db || pb == b;
     if (da && db) return;
-    const uint32_t ga = da ? a : __ldcg(&f[pa]) >> shift;
-    const uint32_t gb = db ? b : __ldcg(&f[pb]) >> shift;
+    const uint32_t ga = da ? a : __ldca(&f[pa]) >> shift;
+    const uint32_t gb = db ? b : __ldca(&f[pb]) >> shift;
     if (!da) {
       if (ga == pa) {
         a = pa;

@@ -164,7 +164,11 @@ constexpr int kFlipUnroll = 4;   // independent sites in flight per thread
 constexpr unsigned kFlipBlocks = 152u * 8u;
 
 // The roots one tile's merge hooked walk to their global root and store
-// (root, marker, root draw) in their own word.
+// (root, marker, root draw) in their own word.  The walks read through L1
+// (they meet on the same upper nodes): the merge is over (its stores are
+// visible after the wait on it), so the only stores racing with a read are
+// these final words, and an older word read in their place points to an
+// ancestor of the same tree.
 __device__ __forceinline__ void compress_tile(const Lattice& lat, uint32_t t) {
   const int sb = lat.sbits, shift = sb + 1;
   const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
@@ -178,7 +182,7 @@ __device__ __forceinline__ void compress_tile(const Lattice& lat, uint32_t t) {
       const uint32_t p = v >> shift;
       if (p == cur) break;
       cur = p;
-      v = __ldcg(&lat.forest[cur]);
+      v = __ldca(&lat.forest[cur]);
     }
     if (it == lat.cap) atomicExch(lat.err, kErrTimeout);
     __stcg(&lat.forest[a], (cur << shift) | lr_bit | (v & dmask));
