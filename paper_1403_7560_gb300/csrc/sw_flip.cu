@@ -16,8 +16,8 @@
 //   its own word.
 // k_apply: every site reads its local root's word (or its own) and writes
 //   its new state (set at random for Ising/Potts, reflection about the
-//   mirror line for XY); global roots are counted.  Ising and Potts states
-//   are bytes: a thread takes four consecutive sites (k_apply_bytes).
+//   mirror line for XY); global roots are counted.  A thread takes four
+//   consecutive sites.
 // k_labels_out: canonical labels (walk to the root) for readout.
 #include <algorithm>
 
@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(S::THREADS, PERSISTENT ? (merge_blocks(S::THRE
 }
 
 constexpr int kFlipThreads = 256, kFlipWarps = kFlipThreads / 32;
-constexpr int kFlipUnroll = 4;   // independent sites in flight per thread
 constexpr unsigned kFlipBlocks = 152u * 8u;
 
 // The roots one tile's merge hooked walk to their global root and store
@@ -227,62 +226,20 @@ __global__ void __launch_bounds__(kFlipThreads, PERSISTENT ? 4 : 6) k_compress_b
   }
 }
 
-// Ising and Potts: every site takes its cluster's draw from its own word
-// (local roots, now compressed) or its local root's word, and its new state
-// is that draw (Ising: 1 = -1).  A thread takes four consecutive sites per
-// step: one 16-byte load of their forest words, one 4-byte store of their
-// states.  The local-root words are read through L1: each of a warp's four
-// gathers (site j of every lane) spans the warp's 128 sites, so the four
-// reach the same lines, and L1 serves the repeats (the forest is read-only
-// in this kernel).
-// All buffers come from the device pool, so 16- and 4-byte accesses are
-// aligned; the last N mod 4 sites are taken one by one.
-template <int MODEL>
-__global__ void __launch_bounds__(kFlipThreads) k_apply_bytes(Lattice lat, uint32_t sweep, Measure mb,
-                                                              bool count) {
-  __shared__ long long s_red[kFlipWarps];
-  pdl_wait();
-  const int sb = lat.sbits, shift = sb + 1;
-  const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
-  const uint32_t nq = lat.N >> 2;
-  const uint4* f4 = reinterpret_cast<const uint4*>(lat.forest);
-  uint32_t* s4 = static_cast<uint32_t*>(lat.spins);
-  auto state = [](uint32_t draw) -> uint32_t { return MODEL == kIsing ? (draw ? 0xffu : 0x01u) : draw; };
-  long long roots = 0;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-    const uint4 w4 = __ldcg(&f4[q]);
-    uint32_t v[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (!(v[j] & lr_bit)) v[j] = __ldg(&lat.forest[v[j] >> shift]);
-      else if ((v[j] >> shift) == 4u * q + (uint32_t)j) ++roots;  // a cluster's root
-    }
-    uint32_t packed = 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) packed |= state(v[j] & dmask) << (8 * j);
-    s4[q] = packed;
-  }
-  if (blockIdx.x == 0 && threadIdx.x < (lat.N & 3u)) {
-    const uint32_t i = 4u * nq + threadIdx.x;
-    uint32_t v = __ldcg(&lat.forest[i]);
-    if (!(v & lr_bit)) v = __ldg(&lat.forest[v >> shift]);
-    else if ((v >> shift) == i) ++roots;
-    static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)state(v & dmask);
-  }
-  if (count) {
-    const long long tot = block_combine<kFlipWarps>(warp_sum(roots), s_red);
-    if (threadIdx.x == 0 && tot)
-      atomicAdd(mb.nclusters + kSlots * (sweep & 1u) + (blockIdx.x % kSlots), (unsigned long long)tot);
-  }
-}
-
-// XY and clock: every site takes its cluster's draw from its own word
-// (local roots, now compressed) or its local root's word; a drawn cluster
-// reflects (XY: about the sweep's mirror line; clock: s -> mirror - s).
+// Every site takes its cluster's draw from its own word (local roots, now
+// compressed) or its local root's word and gets its new state: Ising and
+// Potts take the draw (Ising: 1 = -1); XY and clock reflect a drawn cluster
+// (XY about the sweep's mirror line, clock s -> mirror - s).  A thread takes
+// four consecutive sites per step: one 16-byte load of their forest words,
+// one load and one store of their four states (4, 8 or 16 bytes).  The
+// local-root words are read through L1: each of a warp's four gathers (site
+// j of every lane) spans the warp's 128 sites, so the four reach the same
+// lines, and L1 serves the repeats (the forest is read-only in this kernel).
+// All buffers come from the device pool, so these accesses are aligned; the
+// last N mod 4 sites are taken one by one.
 template <int MODEL>
 __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sweep, Measure mb,
                                                          bool count) {
-  static_assert(MODEL == kXY || MODEL == kClock, "Ising and Potts take k_apply_bytes");
   __shared__ float s_phi;
   __shared__ uint32_t s_mirror;
   __shared__ long long s_red[kFlipWarps];
@@ -296,49 +253,63 @@ __global__ void __launch_bounds__(kFlipThreads) k_apply(Lattice lat, uint32_t sw
   pdl_wait();
   const int sb = lat.sbits, shift = sb + 1;
   const uint32_t lr_bit = 1u << sb, dmask = lr_bit - 1u;
-  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t nq = lat.N >> 2;
+  const uint4* f4 = reinterpret_cast<const uint4*>(lat.forest);
+  // the new state of a site (its state bits) from its old one and its draw
+  auto update = [&](uint32_t old, uint32_t draw) -> uint32_t {
+    if (MODEL == kIsing) return draw ? 0xffu : 0x01u;
+    if (MODEL == kPotts) return draw;
+    if (!draw) return old;
+    if (MODEL == kClock) return (uint32_t)wrap_mod((int)s_mirror - clock_state(old, lat.q), lat.q);
+    const float two_pi = 0x1.921fb6p+2f, pi = 0x1.921fb6p+1f;
+    float t = __fsub_rn(__fadd_rn(__fmul_rn(2.0f, s_phi), pi), __uint_as_float(old));
+    if (t >= two_pi) t = __fsub_rn(t, two_pi);
+    if (t >= two_pi) t = __fsub_rn(t, two_pi);
+    if (t < 0.0f) t = __fadd_rn(t, two_pi);
+    return __float_as_uint(t);
+  };
   long long roots = 0;
-  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < lat.N; base += kFlipUnroll * stride) {
-    uint32_t v[kFlipUnroll];
-    // XY and clock: the old state (angle bits / clock state) is loaded beside
-    // the forest word instead of after the root's word (a shorter load chain)
-    uint32_t old[kFlipUnroll];
-#pragma unroll
-    for (int k = 0; k < kFlipUnroll; ++k) {
-      const uint32_t i = base + k * stride;
-      v[k] = (i < lat.N) ? __ldcg(&lat.forest[i]) : lr_bit;
-      old[k] = 0u;
-      if (MODEL == kXY && i < lat.N) old[k] = __float_as_uint(__ldcg(&static_cast<const float*>(lat.spins)[i]));
-      if (MODEL == kClock && i < lat.N) old[k] = __ldcg(&static_cast<const uint16_t*>(lat.spins)[i]);
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const uint4 w4 = __ldcg(&f4[q]);
+    uint32_t v[4] = {w4.x, w4.y, w4.z, w4.w};
+    // XY and clock: the old states are loaded beside the forest words
+    // rather than after the roots' words (a shorter load chain)
+    uint32_t old[4] = {0u, 0u, 0u, 0u};
+    if (MODEL == kXY) {
+      const uint4 o = __ldcg(&static_cast<const uint4*>(lat.spins)[q]);
+      old[0] = o.x; old[1] = o.y; old[2] = o.z; old[3] = o.w;
+    } else if (MODEL == kClock) {
+      const uint2 o = __ldcg(&static_cast<const uint2*>(lat.spins)[q]);
+      old[0] = o.x & 0xffffu; old[1] = o.x >> 16; old[2] = o.y & 0xffffu; old[3] = o.y >> 16;
     }
 #pragma unroll
-    for (int k = 0; k < kFlipUnroll; ++k) {
-      const uint32_t i = base + k * stride;
-      if (!(v[k] & lr_bit)) v[k] = __ldcg(&lat.forest[v[k] >> shift]);
-      else if (i < lat.N && (v[k] >> shift) == i) ++roots;  // a cluster's root
+    for (int j = 0; j < 4; ++j) {
+      if (!(v[j] & lr_bit)) v[j] = __ldg(&lat.forest[v[j] >> shift]);
+      else if ((v[j] >> shift) == 4u * q + (uint32_t)j) ++roots;  // a cluster's root
     }
+    uint32_t n[4];
 #pragma unroll
-    for (int k = 0; k < kFlipUnroll; ++k) {
-      const uint32_t i = base + k * stride;
-      if (i >= lat.N) continue;
-      const uint32_t draw = v[k] & dmask;
-      if (MODEL == kClock) {
-        if (draw) {
-          uint16_t* sp = static_cast<uint16_t*>(lat.spins);
-          const int q = lat.q;
-          sp[i] = (uint16_t)wrap_mod((int)s_mirror - clock_state(old[k], q), q);
-        }
-      } else if (draw) {
-        float* th = static_cast<float*>(lat.spins);
-        const float phi = s_phi;
-        const float two_pi = 0x1.921fb6p+2f, pi = 0x1.921fb6p+1f;
-        float t = __fsub_rn(__fadd_rn(__fmul_rn(2.0f, phi), pi), __uint_as_float(old[k]));
-        if (t >= two_pi) t = __fsub_rn(t, two_pi);
-        if (t >= two_pi) t = __fsub_rn(t, two_pi);
-        if (t < 0.0f) t = __fadd_rn(t, two_pi);
-        th[i] = t;
-      }
+    for (int j = 0; j < 4; ++j) n[j] = update(old[j], v[j] & dmask);
+    if (MODEL == kXY) {
+      static_cast<uint4*>(lat.spins)[q] = make_uint4(n[0], n[1], n[2], n[3]);
+    } else if (MODEL == kClock) {
+      static_cast<uint2*>(lat.spins)[q] = make_uint2(n[0] | (n[1] << 16), n[2] | (n[3] << 16));
+    } else {
+      static_cast<uint32_t*>(lat.spins)[q] = n[0] | (n[1] << 8) | (n[2] << 16) | (n[3] << 24);
     }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (lat.N & 3u)) {
+    const uint32_t i = 4u * nq + threadIdx.x;
+    uint32_t v = __ldcg(&lat.forest[i]);
+    uint32_t old = 0u;
+    if (MODEL == kXY) old = __ldcg(&static_cast<const uint32_t*>(lat.spins)[i]);
+    if (MODEL == kClock) old = __ldcg(&static_cast<const uint16_t*>(lat.spins)[i]);
+    if (!(v & lr_bit)) v = __ldg(&lat.forest[v >> shift]);
+    else if ((v >> shift) == i) ++roots;
+    const uint32_t n = update(old, v & dmask);
+    if (MODEL == kXY) static_cast<uint32_t*>(lat.spins)[i] = n;
+    else if (MODEL == kClock) static_cast<uint16_t*>(lat.spins)[i] = (uint16_t)n;
+    else static_cast<uint8_t*>(lat.spins)[i] = (uint8_t)n;
   }
   if (count) {
     const long long tot = block_combine<kFlipWarps>(warp_sum(roots), s_red);
@@ -474,18 +445,15 @@ cudaError_t launch_merge(const Lattice& lat, cudaStream_t st) {
 
 cudaError_t launch_flip(const Lattice& lat, int model, uint32_t sweep, const Measure& m, bool count,
                         uint32_t finalize, cudaStream_t st) {
-  // byte states: a thread per four sites; XY and clock: kFlipUnroll sites
-  // in flight per thread; at most kFlipBlocks CTAs striding over the sites
-  const bool bytes = model == kIsing || model == kPotts;
-  const uint32_t per_block = bytes ? 4u * kFlipThreads : (uint32_t)(kFlipThreads * kFlipUnroll);
-  unsigned g = (unsigned)((lat.N + per_block - 1) / per_block);
+  // a thread per four sites; at most kFlipBlocks CTAs striding over them
+  unsigned g = (unsigned)((lat.N + 4u * kFlipThreads - 1) / (4u * kFlipThreads));
   if (g > kFlipBlocks) g = kFlipBlocks;
   if (g == 0) g = 1;
   const unsigned ntiles = (unsigned)(lat.ntx * lat.nty * lat.ntz);
   const cudaError_t e = launch_pdl(k_compress, ntiles, kFlipThreads, st, lat, m, finalize);
   if (e != cudaSuccess) return e;
-  if (model == kIsing) return launch_pdl(k_apply_bytes<kIsing>, g, kFlipThreads, st, lat, sweep, m, count);
-  if (model == kPotts) return launch_pdl(k_apply_bytes<kPotts>, g, kFlipThreads, st, lat, sweep, m, count);
+  if (model == kIsing) return launch_pdl(k_apply<kIsing>, g, kFlipThreads, st, lat, sweep, m, count);
+  if (model == kPotts) return launch_pdl(k_apply<kPotts>, g, kFlipThreads, st, lat, sweep, m, count);
   if (model == kClock) return launch_pdl(k_apply<kClock>, g, kFlipThreads, st, lat, sweep, m, count);
   return launch_pdl(k_apply<kXY>, g, kFlipThreads, st, lat, sweep, m, count);
 }

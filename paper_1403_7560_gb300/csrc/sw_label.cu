@@ -777,15 +777,23 @@ cudaError_t launch_bonds_xy(const Lattice& lat, uint32_t sweep, const Measure* m
   const uint32_t nb = (lat.dim == 2)
                           ? (uint32_t)lat.W * (uint32_t)((lat.L + XYBlock<2>::BY - 1) / XYBlock<2>::BY)
                           : (uint32_t)lat.W * ny * (uint32_t)((lat.L + XYBlock<3>::BZ - 1) / XYBlock<3>::BZ);
-  const unsigned g = nb < (uint32_t)kMeasureBlocks ? (nb ? nb : 1u) : (unsigned)kMeasureBlocks;
+  // one wave: the CTAs the GPU holds at once (the box of projections and the
+  // registers allow five per SM), each striding over the blocks; at most
+  // kMeasureBlocks (the slots of the XY partials)
+  unsigned g = 0;
+  auto launch = [&](auto kernel, const Measure& mm) {
+    g = batch_grid(kernel, 256, nb);
+    if (g > (unsigned)kMeasureBlocks) g = (unsigned)kMeasureBlocks;
+    return launch_pdl(kernel, g, 256, st, lat, sweep, mm);
+  };
   cudaError_t e = cudaSuccess;
   const Measure none{};
   if (lat.dim == 2) {
-    if (m) e = launch_pdl(k_bonds_xy<2, true>, g, 256, st, lat, sweep, *m);
-    else e = launch_pdl(k_bonds_xy<2, false>, g, 256, st, lat, sweep, none);
+    if (m) e = launch(k_bonds_xy<2, true>, *m);
+    else e = launch(k_bonds_xy<2, false>, none);
   } else {
-    if (m) e = launch_pdl(k_bonds_xy<3, true>, g, 256, st, lat, sweep, *m);
-    else e = launch_pdl(k_bonds_xy<3, false>, g, 256, st, lat, sweep, none);
+    if (m) e = launch(k_bonds_xy<3, true>, *m);
+    else e = launch(k_bonds_xy<3, false>, none);
   }
   if (blocks) *blocks = (int)g;
   return e;
