@@ -101,7 +101,8 @@ def test_larger_3d_lattices_bit_exact(sw, model, L, q, T, sweeps):
 
 @pytest.mark.parametrize("dim,L,q,T", [
     (2, 32, 512, 0.9), (2, 48, 8, 1.0), (2, 37, 3, 0.7), (3, 16, 512, 2.2), (3, 20, 6, 2.0),
-    (3, 9, 1024, 2.1), (2, 40, 16, 0.15), (3, 24, 512, 0.3), (2, 40, 64, 50.0), (2, 300, 8, 0.9)])
+    (3, 9, 1024, 2.1), (2, 40, 16, 0.15), (3, 24, 512, 0.3), (2, 40, 64, 50.0), (2, 300, 8, 0.9),
+    (3, 15, 16, 2.0)])
 def test_clock_sweeps_bit_exact(sw, dim, L, q, T):
     """The q-state clock model (the paper's discretised XY): trajectories and
     float moments are reproducible bit for bit, from far below to far above
@@ -417,7 +418,8 @@ def xy_borderline(model_T, dim, L, seed, k, theta, gpu_mask, ora_mask):
 
 
 @pytest.mark.parametrize("dim,L,T,sweeps", [(2, 64, 0.89, 8), (3, 32, 2.2, 6), (3, 48, 2.0, 4),
-                                            (2, 37, 1.1, 6), (3, 64, 2.2, 3), (2, 512, 0.89, 3)])
+                                            (2, 37, 1.1, 6), (3, 64, 2.2, 3), (2, 512, 0.89, 3),
+                                            (3, 11, 2.2, 6)])
 def test_xy_sweeps(sw, dim, L, T, sweeps):
     seed = 3000 + L
     h = sw.sw_create(XY, dim, L, 2, T, seed)
