@@ -361,7 +361,7 @@ int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep);
  * these calls so that the transfers overlap the sweeps.  Host buffers must
  * be page-locked (cudaHostAlloc / pinned) and stay valid, and for uploads
  * unchanged, until sw_wait_io or sw_sync returns.  The handle creates two
- * copy streams and two device buffers of sw_spin_bytes on first use (not
+ * copy streams and one device buffer of sw_spin_bytes on first use (not
  * counted by sw_device_bytes).  Not available for a lattice in a batch
  * (SW_ERR_BAD_ARG).
  *
@@ -369,10 +369,10 @@ int sw_batch_autotune(sw_batch* b, int sweeps, float* ms_per_sweep);
  *     sweeps enqueued afterwards start from it.  The measurement pending on
  *     the replaced state is taken first, as in sw_set_spins.
  * sw_get_spins_async(h, host, bytes)  enqueues the download of the state
- *     after the sweeps enqueued so far: a device-side snapshot, then the
- *     host copy, both on the download stream; later sweeps run meanwhile
- *     and only the next write of the snapshotted buffer waits for the
- *     snapshot (not for the host copy).
+ *     after the sweeps enqueued so far: the state buffer is copied to the
+ *     host on the download stream; later sweeps run meanwhile (they only
+ *     read it until their flip), and the next write of that buffer (a
+ *     flip, an upload into it, sw_set_spins) waits for the copy.
  * sw_get_record_async(h, sweep, host) enqueues the download of the record of
  *     a measured sweep (1 <= sweep <= sw_sweep_counter and among the last
  *     sw_series_capacity sweeps, else SW_ERR_RANGE) into one sw_record; the

@@ -264,7 +264,7 @@ cudaError_t one_sweep(sw_handle* h, uint32_t k, bool measure, cudaEvent_t* ev) {
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], h->stream);
   if (e == cudaSuccess) e = swgb::launch_merge(h->lat, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], h->stream);
-  // the flip writes the spins: a download's snapshot of them goes first
+  // the flip writes the spins: a download of them goes first
   if (e == cudaSuccess) e = swgb::guard_state_write(h, h->lat.spins, h->stream);
   if (e == cudaSuccess) e = swgb::launch_flip(h->lat, h->model, k, h->meas, measure, finalize, h->stream);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->stream);

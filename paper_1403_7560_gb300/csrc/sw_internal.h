@@ -259,7 +259,7 @@ cudaError_t wait_io(sw_handle* h);
 // Frees the asynchronous I/O streams, events and buffers.
 void release_io(sw_handle* h);
 // Called before any work enqueued on stream st writes the spin buffer buf:
-// if a download's snapshot of buf may still be in flight, st waits for it.
+// if a download of buf may still be in flight, st waits for it.
 cudaError_t guard_state_write(sw_handle* h, const void* buf, cudaStream_t st);
 
 }  // namespace swgb
@@ -284,16 +284,15 @@ struct sw_handle {
   struct sw_batch* batch = nullptr;  // batch the lattice belongs to, if any
   // asynchronous host I/O (sw_io.cu), created on first use: an upload and a
   // download stream, the upload target (swapped with lat.spins when the
-  // upload is installed) and the download snapshot, with their events; the
-  // two spin buffers (lat.spins and stage_in in either order) each have an
-  // event marking the end of their last snapshot and a flag saying that no
-  // write has waited for it yet
+  // upload is installed), with their events; the two spin buffers
+  // (lat.spins and stage_in in either order) each have an event marking the
+  // end of their last download and a flag saying that no write has waited
+  // for it yet
   cudaStream_t io_in = nullptr, io_out = nullptr;
   void* stage_in = nullptr;
-  void* snap = nullptr;
   void* io_buf[2] = {nullptr, nullptr};
   cudaEvent_t ev_in_done = nullptr, ev_in_free = nullptr, ev_state = nullptr, ev_rec = nullptr;
-  cudaEvent_t ev_snap[2] = {nullptr, nullptr};
-  bool snap_wait[2] = {false, false};
+  cudaEvent_t ev_down[2] = {nullptr, nullptr};
+  bool down_wait[2] = {false, false};
   bool in_free_set = false;
 };

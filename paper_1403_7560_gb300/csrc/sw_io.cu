@@ -5,19 +5,19 @@
 // off the sweep's critical path.  Uploads run on their own stream into a
 // staging buffer that is swapped with the state buffer once the upload is
 // done (kernels launched afterwards read the new state); downloads copy the
-// state into a snapshot buffer and from there to the host, both on a second
-// stream, so the sweeps go on while the download runs.  Events order the
-// three streams:
+// state buffer itself to the host on a second stream, so the sweeps go on
+// while the download runs (they only read the buffer until the next flip,
+// and the flip waits for the copy).  Events order the three streams:
 //   upload k:   io_in waits ev_in_free (the buffer it fills is no longer
-//               read) and, if the buffer was snapshotted since its last
-//               write, that snapshot; copies, records ev_in_done; the
+//               read) and, if the buffer was downloaded since its last
+//               write, that download; copies, records ev_in_done; the
 //               compute stream waits ev_in_done, the buffers are swapped,
 //               ev_in_free is recorded.
 //   download k: the compute stream records ev_state (the state is final);
-//               io_out waits for it, copies the state to the snapshot
-//               (device to device), records ev_snap of that buffer, copies
-//               the snapshot to the host.  The next write of the buffer, on
-//               any stream, first waits for ev_snap (guard_state_write).
+//               io_out waits for it, copies the state buffer to the host and
+//               records ev_down of that buffer.  The next write of the
+//               buffer, on any stream, first waits for ev_down
+//               (guard_state_write).
 //   record:     the compute stream records ev_rec once the record is final;
 //               io_out waits ev_rec and copies it (small copies issued on
 //               the compute stream would queue behind a download on the
@@ -44,10 +44,9 @@ cudaError_t ensure_io(sw_handle* h) {
   cudaError_t e = cudaStreamCreateWithFlags(&h->io_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = swgb::dev_alloc(&h->stage_in, h->spin_bytes, h->stream);
-  if (e == cudaSuccess) e = swgb::dev_alloc(&h->snap, h->spin_bytes, h->stream);
   // the copy streams use the buffers: order them after the allocations
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaEvent_t* evs[6] = {&h->ev_in_done, &h->ev_in_free, &h->ev_state, &h->ev_rec, &h->ev_snap[0], &h->ev_snap[1]};
+  cudaEvent_t* evs[6] = {&h->ev_in_done, &h->ev_in_free, &h->ev_state, &h->ev_rec, &h->ev_down[0], &h->ev_down[1]};
   for (cudaEvent_t* ev : evs)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -71,11 +70,11 @@ int check_io_args(sw_handle* h, const void* host, size_t bytes) {
 
 cudaError_t swgb::guard_state_write(sw_handle* h, const void* buf, cudaStream_t st) {
   for (int i = 0; i < 2; ++i) {
-    if (!h->snap_wait[i] || buf != h->io_buf[i]) continue;
+    if (!h->down_wait[i] || buf != h->io_buf[i]) continue;
     // later writes of the buffer are ordered after this one: on st itself,
     // or on the other stream through the upload/swap events
-    h->snap_wait[i] = false;
-    return cudaStreamWaitEvent(st, h->ev_snap[i], 0);
+    h->down_wait[i] = false;
+    return cudaStreamWaitEvent(st, h->ev_down[i], 0);
   }
   return cudaSuccess;
 }
@@ -84,22 +83,21 @@ cudaError_t swgb::wait_io(sw_handle* h) {
   cudaError_t e = cudaSuccess;
   if (h->io_in) e = cudaStreamSynchronize(h->io_in);
   if (e == cudaSuccess && h->io_out) e = cudaStreamSynchronize(h->io_out);
-  if (e == cudaSuccess) h->snap_wait[0] = h->snap_wait[1] = false;
+  if (e == cudaSuccess) h->down_wait[0] = h->down_wait[1] = false;
   return e;
 }
 
 void swgb::release_io(sw_handle* h) {
   if (h->io_in) cudaStreamSynchronize(h->io_in);
   if (h->io_out) cudaStreamSynchronize(h->io_out);
-  cudaEvent_t evs[6] = {h->ev_in_done, h->ev_in_free, h->ev_state, h->ev_rec, h->ev_snap[0], h->ev_snap[1]};
+  cudaEvent_t evs[6] = {h->ev_in_done, h->ev_in_free, h->ev_state, h->ev_rec, h->ev_down[0], h->ev_down[1]};
   for (cudaEvent_t ev : evs)
     if (ev) cudaEventDestroy(ev);
-  h->ev_in_done = h->ev_in_free = h->ev_state = h->ev_rec = h->ev_snap[0] = h->ev_snap[1] = nullptr;
+  h->ev_in_done = h->ev_in_free = h->ev_state = h->ev_rec = h->ev_down[0] = h->ev_down[1] = nullptr;
   swgb::dev_free(h->stage_in, h->stream);
-  swgb::dev_free(h->snap, h->stream);
-  h->stage_in = h->snap = nullptr;
+  h->stage_in = nullptr;
   h->io_buf[0] = h->io_buf[1] = nullptr;
-  h->snap_wait[0] = h->snap_wait[1] = false;
+  h->down_wait[0] = h->down_wait[1] = false;
   if (h->io_in) cudaStreamDestroy(h->io_in);
   if (h->io_out) cudaStreamDestroy(h->io_out);
   h->io_in = h->io_out = nullptr;
@@ -136,12 +134,11 @@ int sw_get_spins_async(sw_handle* h, void* host, size_t bytes) {
   const int b = h->lat.spins == h->io_buf[0] ? 0 : 1;
   if (e == cudaSuccess) e = cudaEventRecord(h->ev_state, h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_state, 0);
-  // the previous download's host copy precedes this snapshot on io_out
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->snap, h->lat.spins, bytes, cudaMemcpyDeviceToDevice, h->io_out);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_snap[b], h->io_out);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host, h->snap, bytes, cudaMemcpyDeviceToHost, h->io_out);
+  // the buffer itself goes to the host; its next write waits for ev_down
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, h->lat.spins, bytes, cudaMemcpyDeviceToHost, h->io_out);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_down[b], h->io_out);
   if (e != cudaSuccess) return io_cuda(e, "get_spins_async");
-  h->snap_wait[b] = true;
+  h->down_wait[b] = true;
   return SW_OK;
 }
 
