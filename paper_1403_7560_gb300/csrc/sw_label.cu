@@ -119,13 +119,15 @@ __device__ __forceinline__ void measure_row(const RowBytes& rb, uint32_t e0, uin
 // MM (measurement mode) 1 = Ising, 2 = Potts: also measure the incoming
 // spins (the state after sweep - 1): M and E from the row words' equality
 // masks and the Potts histogram, added to the measurement slots (the flip
-// kernel of this sweep writes the record of sweep - 1).  MM = 0: none.
+// kernel of this sweep writes the record of sweep - 1).  MM 0 and 3: no
+// measurement, two-state (0: Ising, and XY / clock from their bond planes)
+// or Potts (3) cluster draws.
 // Shared memory of one tile's labeling in measurement mode MM (the Potts
 // draw words and histograms only where Potts lattices can run).
 template <class S, int MM>
 struct LabelSmem {
   static constexpr int ROWS = S::ROWS, NW = S::THREADS / 32;
-  static constexpr bool kPottsDraws = MM != 1;  // MM 1: Ising only (two-state draws)
+  static constexpr bool kPottsDraws = MM >= 2;  // MM 0 and 1: two-state draws only
   static constexpr int kDrawWords = (kPottsDraws ? 8 : 1) * (ROWS + 1);
   static constexpr int kHist = MM == 2 ? 256 : 1, kWHist = MM == 2 ? NW * kSmallQ : 1;
   alignas(16) uint32_t par[ROWS * 32];
@@ -144,7 +146,7 @@ struct LabelSmem {
 template <class Sh, bool FROM_MASK, int MM, class Smem>
 __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, uint32_t sweep,
                                            const Measure& mb, Smem& sm) {
-  constexpr bool MEASURE = MM != 0;
+  constexpr bool MEASURE = MM == 1 || MM == 2;
   constexpr int D = Sh::D, TY = Sh::TY, TZ = Sh::TZ, ROWS = Sh::ROWS, NT = Sh::THREADS;
   constexpr int NW = NT / 32, RPW = ROWS / NW;
   static_assert(ROWS == NT && NT % 32 == 0, "one thread per row word, whole warps");
@@ -213,7 +215,7 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
       const uint32_t e0 = eq_bits(rb.a, rb.ax) & vmask;
       const uint32_t e1 = eq_bits(rb.a, rb.ay) & vmask;
       const uint32_t e2 = (D == 3) ? (eq_bits(rb.a, rb.az) & vmask) : 0u;
-      if (MM != 0) measure_row<D, MM>(rb, e0, e1, e2, vmask, nvalid, lat.q, m_acc, e_acc, s_whist + warp * kSmallQ, s_hist);
+      if (MEASURE) measure_row<D, MM>(rb, e0, e1, e2, vmask, nvalid, lat.q, m_acc, e_acc, s_whist + warp * kSmallQ, s_hist);
       A0 = e0 ? (e0 & bernoulli_word(g, sweep, 0, lat.t_bond, e0, lat.rk)) : 0u;
       A1 = e1 ? (e1 & bernoulli_word(g, sweep, 1, lat.t_bond, e1, lat.rk)) : 0u;
       if (D == 3) A2 = e2 ? (e2 & bernoulli_word(g, sweep, 2, lat.t_bond, e2, lat.rk)) : 0u;
@@ -684,19 +686,29 @@ void tiles_for(int dim, int L, int* ntx, int* nty, int* ntz, int shape) {
   *ntz = (dim == 2) ? 1 : (L + tz - 1) / tz;
 }
 
-cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st) {
-  const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz);
-  cudaError_t e = cudaSuccess;
+namespace {
+template <int D>
+cudaError_t launch_label_dim(const Lattice& lat, uint32_t sweep, bool from_mask, bool potts_draws,
+                             cudaStream_t st) {
+  const unsigned g = (unsigned)(lat.ntx * lat.nty * lat.ntz), t = (unsigned)Tile<D>::THREADS;
   const Measure none{};
-  if (lat.dim == 2) {
-    if (from_mask) e = launch_pdl(k_label<2, true, 0>, g, (unsigned)Tile<2>::THREADS, st, lat, sweep, none);
-    else e = launch_pdl(k_label<2, false, 0>, g, (unsigned)Tile<2>::THREADS, st, lat, sweep, none);
-  } else {
-    if (from_mask) e = launch_pdl(k_label<3, true, 0>, g, (unsigned)Tile<3>::THREADS, st, lat, sweep, none);
-    else e = launch_pdl(k_label<3, false, 0>, g, (unsigned)Tile<3>::THREADS, st, lat, sweep, none);
+  if (from_mask) {
+    if (potts_draws) return launch_pdl(k_label<D, true, 3>, g, t, st, lat, sweep, none);
+    return launch_pdl(k_label<D, true, 0>, g, t, st, lat, sweep, none);
   }
-  return e;
+  if (potts_draws) return launch_pdl(k_label<D, false, 3>, g, t, st, lat, sweep, none);
+  return launch_pdl(k_label<D, false, 0>, g, t, st, lat, sweep, none);
 }
+}  // namespace
+
+cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cudaStream_t st) {
+  // the Potts layout (a draw byte per site in shared memory) only where
+  // Potts draws are made; two-state draws or none take the smaller layout
+  const bool potts_draws = sweep != 0u && lat.dq != 2;
+  if (lat.dim == 2) return launch_label_dim<2>(lat, sweep, from_mask, potts_draws, st);
+  return launch_label_dim<3>(lat, sweep, from_mask, potts_draws, st);
+}
+
 
 namespace {
 
