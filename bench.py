@@ -246,6 +246,67 @@ def cpu_baseline_xy(sweeps: int = 2, warm: int = 1):
                       f"{dt:.1f} s on one host core"}
 
 
+def _oracle_ready(_):
+    import oracle  # noqa: F401  (the worker loads the oracle library once)
+    return 0
+
+
+def _oracle_job(spec):
+    """One job of the host-core baseline: create the oracle lattice and run
+    `sweeps` sweeps; returns (site updates, seconds)."""
+    import oracle
+    model, dim, L_, q, T_, seed, sweeps = spec
+    t0 = time.perf_counter()
+    o = oracle.Oracle(model, dim, L_, q, T_, seed)
+    o.sweep(sweeps)
+    o.close()
+    return L_ ** dim * sweeps, time.perf_counter() - t0
+
+
+def cpu_baseline_jobs(specs, what):
+    """The oracle on independent jobs (model, dim, L, q, T, seed, sweeps)
+    across every host core: a spawn-context pool (the process has CUDA
+    initialised, so no fork), started and warmed before the clock; the
+    largest jobs first.  Aggregate site-updates/ns over the pool's wall
+    time, lattice creation included."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    order = sorted(specs, key=lambda s: -(s[2] ** s[1]) * s[6])
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_ready, range(cores), chunksize=1)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_job, order, chunksize=1)
+        wall = time.perf_counter() - t0
+    su = sum(r[0] for r in res)
+    return {"value": su / (wall * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what}; {su / 1e6:.1f} M site updates in {wall:.1f} s on {cores} host cores"}
+
+
+def batch_specs():
+    import inputs
+    return inputs.ragged_batch(256, 1003)
+
+
+def serve_specs(args, max_l2, max_l3, max_sweeps):
+    import inputs
+    return inputs.served_stream(args.jobs, 1004, max_L2=max_l2, max_L3=max_l3, sweeps=(100, max_sweeps))
+
+
+def leg_baselines(args, line, sweeps=3):
+    """Host-core oracle baselines of the batch and serve legs in `line`."""
+    if "batch" in line:
+        specs = [s + (sweeps,) for s in batch_specs()]
+        line["batch"]["cpu_baseline"] = cpu_baseline_jobs(
+            specs, f"the 256 lattices of the ragged batch, {sweeps} sweeps each from creation")
+    for key, lims in (("serve", (args.max_l2, args.max_l3, args.max_sweeps)), ("serve_small_jobs", (1024, 128, 1000))):
+        if key in line:
+            jobs = serve_specs(args, *lims)
+            specs = [(j["model"], j["dim"], j["L"], j["q"], j["T"], j["seed"], min(sweeps, j["sweeps"])) for j in jobs]
+            line[key]["cpu_baseline"] = cpu_baseline_jobs(
+                specs, f"the {len(jobs)} jobs of the stream, {sweeps} sweeps each from creation (not their "
+                       f"full sweep counts)")
+
+
 def run_reference(args):
     # the oracle runs once, on rank 0; other ranks have nothing to do
     if int(os.environ.get("RANK", "0")) != 0:
@@ -496,6 +557,7 @@ def run_gpu(args):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sweeps)
             line["other_workloads"]["xy3d_L256"]["cpu_baseline"] = cpu_baseline_xy()
+            leg_baselines(args, line)
         print(json.dumps(line), flush=True)
     sw.sw_destroy(h)
     if world > 1:
@@ -640,6 +702,9 @@ def run_batch(args):
     leg = batch_leg(args, torch.cuda.Stream())
     line = dict(leg, n_gpus=1, warmup=max(args.warmup, 3), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="int8", data="synthetic")
+    if not args.no_cpu_baseline:
+        legs = {"batch": line}
+        leg_baselines(args, legs)
     print(json.dumps(line), flush=True)
 
 
@@ -697,6 +762,9 @@ def run_serve(args):
     torch.cuda.set_device(0)
     line = dict(serve_leg(args), n_gpus=1, warmup=1, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="int8/uint8/f32", data="synthetic")
+    if not args.no_cpu_baseline:
+        legs = {"serve": line}
+        leg_baselines(args, legs)
     print(json.dumps(line), flush=True)
 
 

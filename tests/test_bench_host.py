@@ -1,5 +1,6 @@
 """Host-side logic of bench.py on CPU: the multi-rank timing aggregation
-(world size 2 over gloo, the N > 1 replica path) and the clock parser."""
+(world size 2 over gloo, the N > 1 replica path), the clock parser, the
+launch counts and the host-core oracle baseline of the batch and serve legs."""
 from __future__ import annotations
 
 import datetime
@@ -96,3 +97,13 @@ def test_workload_recipes():
             tc = inputs.TC_2D_ISING if model == inputs.ISING else inputs.tc_2d_potts(q)
             assert 0.8 * tc <= T <= 1.2 * tc
     assert inputs.small_batch(8, 7) == inputs.small_batch(8, 7)
+
+
+def test_host_core_oracle_baseline():
+    """The batch/serve legs' oracle baseline: independent jobs on a spawn
+    pool over the host cores, their site updates summed over its wall time."""
+    import bench
+    specs = [(0, 2, 32, 2, 2.269185, 11 + k, 2) for k in range(3)] + [(1, 2, 24, 3, 0.994973, 5, 2)]
+    out = bench.cpu_baseline_jobs(specs, "four small jobs")
+    assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
+    assert "M site updates" in out["sample"] and out["unit"] == bench.UNIT
