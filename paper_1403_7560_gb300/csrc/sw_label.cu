@@ -234,24 +234,37 @@ __device__ __forceinline__ void label_tile(const Lattice& lat, uint32_t tile, ui
     } else if (draws && Smem::kPottsDraws) {
       // Potts cluster draw of every site: word (i & 3) of Philox(i >> 2, sweep, DRAW, 0)
       const uint32_t i0 = row * (uint32_t)L + (uint32_t)tc.x0;
-      uint32_t cached = 0xffffffffu;
-      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t dq = (uint32_t)lat.dq;
+      if ((L & 3) == 0) {
+        // L a multiple of 4 (the same branch for the whole lattice): the row
+        // word starts a Philox group, and group j holds the draws of its
+        // sites 4j..4j+3 (those past the end of the row go unused)
 #pragma unroll 1
-      for (int j = 0; j < 8; ++j) {
-        uint32_t packed = 0u;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int b = 4 * j + t;
-          if (b < nvalid) {
-            const uint32_t i = i0 + (uint32_t)b;
-            if ((i >> 2) != cached) {
-              cached = i >> 2;
-              w = philox(cached, sweep, kDraw, 0u, lat.rk);
-            }
-            packed |= draw_value(word_of(w, (int)(i & 3u)), (uint32_t)lat.dq) << (8 * t);
-          }
+        for (int j = 0; j < 8; ++j) {
+          const uint4 w = philox((i0 >> 2) + (uint32_t)j, sweep, kDraw, 0u, lat.rk);
+          sdraw[j * (ROWS + 1) + r] = draw_value(w.x, dq) | (draw_value(w.y, dq) << 8) |
+                                      (draw_value(w.z, dq) << 16) | (draw_value(w.w, dq) << 24);
         }
-        sdraw[j * (ROWS + 1) + r] = packed;
+      } else {
+        uint32_t cached = 0xffffffffu;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll 1
+        for (int j = 0; j < 8; ++j) {
+          uint32_t packed = 0u;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int b = 4 * j + t;
+            if (b < nvalid) {
+              const uint32_t i = i0 + (uint32_t)b;
+              if ((i >> 2) != cached) {
+                cached = i >> 2;
+                w = philox(cached, sweep, kDraw, 0u, lat.rk);
+              }
+              packed |= draw_value(word_of(w, (int)(i & 3u)), dq) << (8 * t);
+            }
+          }
+          sdraw[j * (ROWS + 1) + r] = packed;
+        }
       }
     }
   }
@@ -708,7 +721,6 @@ cudaError_t launch_label(const Lattice& lat, uint32_t sweep, bool from_mask, cud
   if (lat.dim == 2) return launch_label_dim<2>(lat, sweep, from_mask, potts_draws, st);
   return launch_label_dim<3>(lat, sweep, from_mask, potts_draws, st);
 }
-
 
 namespace {
 
