@@ -1,8 +1,9 @@
 """The serving loop's host logic on CPU, against a fake of the C ABI that
 counts sweeps the way the library does (a batch call advances each member by
-min(n, target - counter)): every job gets exactly its sweeps, XY jobs run
-alone, admission follows arrival order and never exceeds the HBM budget,
-and a job larger than the whole budget is rejected with an error."""
+min(n, target - counter)): every job gets exactly its sweeps, XY jobs and
+large lattices run alone, admission follows arrival order and never exceeds
+the HBM budget, and a job larger than the whole budget is rejected with an
+error."""
 from __future__ import annotations
 
 import os
@@ -151,6 +152,31 @@ def test_groups_advance_independently(serve, monkeypatch):
     assert sorted(j.result["n_sweeps"] for j in done) == [16, 64]
     # the 2D batch got chunks while the 3D batch's first chunk was still running
     assert len(b2.calls) == 8 and len(b3.calls) == 2
+
+
+def test_large_lattices_and_xy_run_alone(serve, monkeypatch):
+    """Lattices of at least solo_sites sites and XY jobs get a group of their
+    own (sw_sweep on their handle); the others join their dimension's batch."""
+    fake = FakeSw(1 << 30)
+    monkeypatch.setattr(serve, "sw", fake)
+    alone, batched = set(), set()
+    sweep, add = fake.sw_sweep, fake.sw_batch_add
+
+    def sw_sweep(h, n):
+        alone.add((h.model, h.dim, h.L))
+        sweep(h, n)
+
+    def sw_batch_add(b, h):
+        batched.add((h.model, h.dim, h.L))
+        add(b, h)
+    fake.sw_sweep, fake.sw_batch_add = sw_sweep, sw_batch_add
+    s = serve.Server(1 << 30, chunk=16, solo_sites=1000)
+    specs = [(0, 2, 40, 50), (0, 2, 20, 50), (1, 3, 12, 30), (1, 3, 9, 40), (2, 3, 8, 20)]
+    done = s.run(jobs(serve, specs), realtime=False)
+    s.close()
+    assert alone == {(0, 2, 40), (1, 3, 12), (2, 3, 8)}      # 1600 and 1728 sites, and XY
+    assert batched == {(0, 2, 20), (1, 3, 9)}                 # 400 and 729 sites
+    assert sorted((j.id, j.result["n_sweeps"]) for j in done) == [(k, n) for k, (_, _, _, n) in enumerate(specs)]
 
 
 def test_summary_percentiles(serve):
