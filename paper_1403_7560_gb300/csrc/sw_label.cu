@@ -420,12 +420,25 @@ __global__ void __launch_bounds__(256) k_measure_rows(const __grid_constant__ La
   const int L = lat.L;
   const uint32_t words = lat.R * (uint32_t)lat.W;
   int m_acc = 0, e_acc = 0;
+  // L a power of two (then so is W): indices by shifts and masks
+  const bool pow2 = (L & (L - 1)) == 0;
+  const int lsh = __ffs(L) - 1, wsh = __ffs(lat.W) - 1;
   for (uint32_t g = blockIdx.x * 256u + threadIdx.x; g < words; g += gridDim.x * 256u) {
-    const uint32_t row = g / (uint32_t)lat.W, tx = g % (uint32_t)lat.W;
+    uint32_t row, tx, y, z;
+    if (pow2) {
+      row = g >> wsh;
+      tx = g & (uint32_t)(lat.W - 1);
+      y = row & (uint32_t)(L - 1);
+      z = row >> lsh;
+    } else {
+      row = g / (uint32_t)lat.W;
+      tx = g % (uint32_t)lat.W;
+      y = row % (uint32_t)L;
+      z = row / (uint32_t)L;
+    }
     const int x0 = 32 * (int)tx;
     const int nvalid = min(32, L - x0);
     const uint32_t vmask = (nvalid >= 32) ? kFull : ((1u << nvalid) - 1u);
-    const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
     const uint32_t y1 = (y + 1u == (uint32_t)L) ? 0u : y + 1u;
     const uint32_t z1 = (D == 3) ? ((z + 1u == (uint32_t)L) ? 0u : z + 1u) : 0u;
     RowBytes rb;
@@ -626,9 +639,23 @@ __global__ void __launch_bounds__(256) k_bonds_clock(const __grid_constant__ Lat
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   long long cx = 0, sy = 0, eb = 0;
+  // L a power of two (then so is W): a row word's indices by shifts and
+  // masks instead of four divisions (the same branch for the whole lattice)
+  const bool pow2 = (L & (L - 1)) == 0;
+  const int lsh = __ffs(L) - 1, wsh = __ffs(lat.W) - 1;
   for (uint32_t g = gw; g < nwords; g += nw) {
-    const uint32_t row = g / (uint32_t)lat.W, xw = g % (uint32_t)lat.W;
-    const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
+    uint32_t row, xw, y, z;
+    if (pow2) {
+      row = g >> wsh;
+      xw = g & (uint32_t)(lat.W - 1);
+      y = row & (uint32_t)(L - 1);
+      z = row >> lsh;
+    } else {
+      row = g / (uint32_t)lat.W;
+      xw = g % (uint32_t)lat.W;
+      y = row % (uint32_t)L;
+      z = row / (uint32_t)L;
+    }
     const int x = (int)(32 * xw) + lane;
     uint32_t a = 0u;
     if (x < L) {

@@ -38,10 +38,23 @@ __device__ __forceinline__ bool plane_bit(const Lattice& lat, int d, uint32_t ro
 template <int D>
 __global__ void __launch_bounds__(kT) k_le_scan(Lattice lat, int32_t* label, int* changed) {
   const int L = lat.L;
+  // L a power of two: a site's coordinates by shifts and masks
+  const bool pow2 = (L & (L - 1)) == 0;
+  const int lsh = __ffs(L) - 1;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < lat.N; i += gridDim.x * blockDim.x) {
-    const int x = (int)(i % (uint32_t)L);
-    const uint32_t row = i / (uint32_t)L;
-    const int y = (int)(row % (uint32_t)L), z = (D == 3) ? (int)(row / (uint32_t)L) : 0;
+    int x, y, z;
+    uint32_t row;
+    if (pow2) {
+      x = (int)(i & (uint32_t)(L - 1));
+      row = i >> lsh;
+      y = (int)(row & (uint32_t)(L - 1));
+      z = (D == 3) ? (int)(row >> lsh) : 0;
+    } else {
+      x = (int)(i % (uint32_t)L);
+      row = i / (uint32_t)L;
+      y = (int)(row % (uint32_t)L);
+      z = (D == 3) ? (int)(row / (uint32_t)L) : 0;
+    }
     const int32_t l = __ldcg(&label[i]);
     int32_t m = l;
     // +d neighbours (bond owned by i) and -d neighbours (bond owned by them)
