@@ -54,6 +54,19 @@ struct SmallScratch {
   double s_acc[6];  // the FP64 accumulators, written back at the end
 };
 
+// Division by an invariant divisor d (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", 1994): with m = floor((2^32 -
+// 1) / d) + 1, floor(n / d) = umulhi(n, m) whenever n * d < 2^32 (the
+// product overshoots n / d by less than n / 2^32 < 1 / d, which cannot
+// carry the quotient past the next integer); d = 1 takes n itself.  The
+// small lattices' indices (n <= 3 N, d <= N, N <= 8192) are far inside.
+struct InvDiv {
+  uint32_t d, m;
+  __device__ explicit InvDiv(uint32_t dv) : d(dv), m(dv > 1u ? 0xffffffffu / dv + 1u : 0u) {}
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return d > 1u ? __umulhi(n, m) : n; }
+  __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+};
+
 // n sweeps after sweep0 of one small lattice by the whole CTA.
 template <int D, bool POTTS>
 __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& mb, uint32_t sweep0, int n,
@@ -69,6 +82,7 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
   uint8_t* sp = smem + lay.spins;
   uint8_t* pd = smem + lay.pdraw;
   const uint32_t N = lat.N, L = (uint32_t)lat.L, W = (uint32_t)lat.W, RW = lat.R * W;
+  const InvDiv byL(L), byW(W), byRW(RW);
   const uint32_t tid = threadIdx.x;
   const int q = lat.q, sb = lat.sbits, shift = sb + 1;
   const bool two_state = lat.dq == 2;
@@ -84,8 +98,8 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
     __syncthreads();
     // step (1a): equality masks, a warp per row word (lane per site, ballots)
     for (uint32_t g = warp; g < RW; g += kSmallWarps) {
-      const uint32_t row = g / W, x = 32u * (g % W) + lane;
-      const uint32_t y = row % L, z = row / L;
+      const uint32_t row = byW.div(g), x = 32u * (g - row * W) + lane;
+      const uint32_t z = byL.div(row), y = row - z * L;
       bool q0 = false, q1 = false, q2 = false;
       if (x < L) {
         const uint8_t si = sp[row * L + x];
@@ -100,7 +114,7 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
     // step (1b): Bernoulli words, a thread per (row word, direction); the
     // two-state draw words
     for (uint32_t c = tid; c < (uint32_t)D * RW; c += kSmallThreads) {
-      const uint32_t d = c / RW, g = c % RW;
+      const uint32_t d = byRW.div(c), g = c - d * RW;
       const uint32_t e = pl[c];
       pl[c] = e ? (e & bernoulli_word(g, sweep, (int)d, lat.t_bond, e, lat.rk)) : 0u;
     }
@@ -119,7 +133,7 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
     // step (2a): every site's parent is the start of its x-run inside its
     // row word (a warp per row word, lane per site)
     for (uint32_t g = warp; g < RW; g += kSmallWarps) {
-      const uint32_t row = g / W, x0 = 32u * (g % W);
+      const uint32_t row = byW.div(g), x0 = 32u * (g - row * W);
       const int nvalid = (int)min(32u, L - x0);
       const uint32_t vmask = nvalid >= 32 ? kFull : ((1u << nvalid) - 1u);
       const uint32_t S = ~((pl[g] & (vmask >> 1)) << 1) & vmask;
@@ -131,8 +145,8 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
     // word along x (or around), to the +y row and to the +z row; runs
     // already joined through the previous bit are skipped
     for (uint32_t g = tid; g < RW; g += kSmallThreads) {
-      const uint32_t row = g / W, xw = g % W, x0 = 32u * xw;
-      const uint32_t y = row % L, z = row / L;
+      const uint32_t row = byW.div(g), xw = g - row * W, x0 = 32u * xw;
+      const uint32_t z = byL.div(row), y = row - z * L;
       const int nvalid = (int)min(32u, L - x0);
       const uint32_t vmask = nvalid >= 32 ? kFull : ((1u << nvalid) - 1u);
       const uint32_t A0 = pl[g], X = A0 & (vmask >> 1), S = ss[g], base = row * L + x0;
@@ -160,12 +174,12 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
     // step (3): every site takes its root's draw; roots counted
     long long roots = 0;
     for (uint32_t g = warp; g < RW; g += kSmallWarps) {
-      const uint32_t row = g / W, x = 32u * (g % W) + lane;
+      const uint32_t row = byW.div(g), x = 32u * (g - row * W) + lane;
       if (x >= L) continue;
       const uint32_t i = row * L + x;
       const uint32_t r = sfind(par, i);
       if (r == i) ++roots;
-      const uint32_t xr = r % L, gr = (r / L) * W + (xr >> 5);
+      const uint32_t rr = byL.div(r), xr = r - rr * L, gr = rr * W + (xr >> 5);
       const uint32_t v = two_state ? (dw[gr] >> (xr & 31u)) & 1u : pd[r];
       sp[i] = POTTS ? (uint8_t)v : (uint8_t)(v ? (int8_t)-1 : (int8_t)1);
       if (last) {
@@ -182,9 +196,9 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
     __syncthreads();
     long long m = 0, en = 0;
     for (uint32_t g = warp; g < RW; g += kSmallWarps) {
-      const uint32_t row = g / W, x = 32u * (g % W) + lane;
+      const uint32_t row = byW.div(g), x = 32u * (g - row * W) + lane;
       if (x >= L) continue;
-      const uint32_t y = row % L, z = row / L, i = row * L + x;
+      const uint32_t z = byL.div(row), y = row - z * L, i = row * L + x;
       uint32_t j[3];
       j[0] = x + 1u == L ? i - x : i + 1u;
       j[1] = y + 1u == L ? i - y * L : i + L;

@@ -74,3 +74,15 @@ def test_xy_exp_estimate_within_its_margin(T):
     pf = (np.float32(1.0) - e).astype(np.float64)
     exact = -np.expm1(-a.astype(np.float64))
     assert (np.abs(pf - exact) + expf_error(-a, e)).max() < 2.0 ** -16 / 8
+
+
+def test_invariant_divisor_multiplication_is_exact_for_small_lattices():
+    """The small-lattice kernel divides by L, W and R*W with the
+    multiply-high of Granlund & Montgomery: m = floor((2^32 - 1) / d) + 1 and
+    floor(n / d) = (n * m) >> 32 for n * d < 2^32.  Every divisor up to the
+    largest small lattice (8192 sites) with every dividend up to three times
+    that (the kernel's largest, D * R * W) gives the exact quotient."""
+    n = np.arange(3 * 8192, dtype=np.uint64)
+    for d in range(2, 8193):
+        m = np.uint64((2 ** 32 - 1) // d + 1)
+        assert np.array_equal((n * m) >> np.uint64(32), n // np.uint64(d)), d
