@@ -49,7 +49,7 @@ __host__ __device__ SmallLayout small_layout(const Lattice& lat, bool potts) {
 
 // Shared memory of a small sweep besides the dynamic lattice block.
 struct SmallScratch {
-  long long s_ri[kSmallWarps];
+  long long s_ri[4 * kSmallWarps];  // per-warp partials of the record's four sums
   unsigned int s_hist[256];
   double s_acc[6];  // the FP64 accumulators, written back at the end
 };
@@ -220,11 +220,18 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
       __syncthreads();
       if (tid < (uint32_t)q) s2 = (long long)s_hist[tid] * (long long)s_hist[tid];
     }
-    const long long M = block_combine<kSmallWarps>(warp_sum(m), s_ri);
-    const long long E = block_combine<kSmallWarps>(warp_sum(en), s_ri);
-    const long long S2 = block_combine<kSmallWarps>(warp_sum(s2), s_ri);
-    const long long ncl = block_combine<kSmallWarps>(warp_sum(roots), s_ri);
-    if (tid == 0) write_record(lat, mb, sweep, M, E, S2, 0.0, 0.0, 0.0, ncl, s_acc);
+    // the four sums in one block reduction (two barriers instead of eight:
+    // the whole lattice is on one SM, so every barrier is on the critical path)
+    const long long part[4] = {warp_sum(m), warp_sum(en), warp_sum(s2), warp_sum(roots)};
+    __syncthreads();
+    if (lane == 0)
+      for (int k = 0; k < 4; ++k) s_ri[k * kSmallWarps + warp] = part[k];
+    __syncthreads();
+    if (warp == 0) {
+      long long tot[4];
+      for (int k = 0; k < 4; ++k) tot[k] = warp_sum(s_ri[k * kSmallWarps + lane]);
+      if (lane == 0) write_record(lat, mb, sweep, tot[0], tot[1], tot[2], 0.0, 0.0, 0.0, tot[3], s_acc);
+    }
   }
   __syncthreads();
   uint8_t* out = static_cast<uint8_t*>(lat.spins);
