@@ -574,11 +574,10 @@ def batch_launches(specs, schedule):
     """Kernels one batch sweep launches: the tiled members' labels (one
     launch per model under label layout 0, one in all under layout 1 -- bit 0
     of the schedule), merge (one launch, or one per axis under bit 2),
-    compression and apply; one launch per model of the small members (2D
-    Ising up to 4096 sites, 2D Potts up to 8192, 3D up to 1024); the step
-    counter."""
+    compression and apply; one launch per model of the small members (2D up
+    to 8192 sites, 3D up to 4096); the step counter."""
     def is_small(m, d, L):
-        return L ** d <= ((8192 if m == 1 else 4096) if d == 2 else 1024)
+        return L ** d <= (8192 if d == 2 else 4096)
     tiled = {m for (m, d, L, _, _, _) in specs if not is_small(m, d, L)}
     small = {m for (m, d, L, _, _, _) in specs if is_small(m, d, L)}
     labels = (len(tiled) if (schedule & 1) == 0 else 1) if tiled else 0

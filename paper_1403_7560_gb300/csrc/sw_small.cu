@@ -1,6 +1,6 @@
-// Small Ising/Potts lattices (N <= small_sites_limit: 2D Ising 4096, 2D
-// Potts 8192, 3D 1024): whole sweeps by one CTA with the lattice in shared
-// memory, n sweeps per launch.
+// Small Ising/Potts lattices (N <= small_sites_limit: 2D 8192, 3D 4096):
+// whole sweeps by one CTA with the lattice in shared memory, n sweeps per
+// launch.
 //
 // The tiled path pays four kernel launches and a global merge per sweep,
 // which for a lattice of a few thousand sites is nearly all of the time.
@@ -83,6 +83,13 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
   uint8_t* pd = smem + lay.pdraw;
   const uint32_t N = lat.N, L = (uint32_t)lat.L, W = (uint32_t)lat.W, RW = lat.R * W;
   const InvDiv byL(L), byW(W), byRW(RW);
+  // the unions of a row word are split by bit range over 2^segsh threads:
+  // the largest power of two up to 16 whose threads for all row words stay
+  // within about one CTA (a thread then walks at most 32 >> segsh unions
+  // of a row word, instead of all of them)
+  uint32_t segsh = 0;
+  while (segsh < 4u && (RW << (segsh + 1u)) <= kSmallThreads + kSmallThreads / 8u) ++segsh;
+  const uint32_t segb = 32u >> segsh, segbits = segb == 32u ? kFull : (1u << segb) - 1u;
   const uint32_t tid = threadIdx.x;
   const int q = lat.q, sb = lat.sbits, shift = sb + 1;
   const bool two_state = lat.dq == 2;
@@ -141,16 +148,19 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
       if ((int)lane < nvalid) par[row * L + x0 + lane] = row * L + x0 + run_start(S, (int)lane);
     }
     __syncthreads();
-    // step (2b): a thread per row word joins the runs bonded to the next row
-    // word along x (or around), to the +y row and to the +z row; runs
-    // already joined through the previous bit are skipped
-    for (uint32_t g = tid; g < RW; g += kSmallThreads) {
+    // step (2b): threads per row word (one per bit range) join the runs
+    // bonded to the +y row and to the +z row; runs already joined through
+    // the previous bit are skipped; the last range's thread also joins the
+    // run bonded to the next row word along x (or around)
+    for (uint32_t c = tid; c < (RW << segsh); c += kSmallThreads) {
+      const uint32_t g = c >> segsh, seg = c & ((1u << segsh) - 1u);
+      const uint32_t segmask = segbits << (segb * seg);
       const uint32_t row = byW.div(g), xw = g - row * W, x0 = 32u * xw;
       const uint32_t z = byL.div(row), y = row - z * L;
       const int nvalid = (int)min(32u, L - x0);
       const uint32_t vmask = nvalid >= 32 ? kFull : ((1u << nvalid) - 1u);
       const uint32_t A0 = pl[g], X = A0 & (vmask >> 1), S = ss[g], base = row * L + x0;
-      if ((A0 >> (nvalid - 1)) & 1u) {
+      if (seg == (1u << segsh) - 1u && ((A0 >> (nvalid - 1)) & 1u)) {
         const uint32_t i = base + (uint32_t)(nvalid - 1);
         sunion(par, base + run_start(S, nvalid - 1), x0 + (uint32_t)nvalid == L ? row * L : i + 1u, lat.err,
                lat.cap);
@@ -162,7 +172,7 @@ __device__ __forceinline__ void sweep_small(const Lattice& lat, const Measure& m
         const uint32_t gn = rown * W + xw, Yd = pl[d * RW + g];
         if (!Yd) continue;
         const uint32_t Xn = pl[gn] & (vmask >> 1), Sn = ss[gn], basen = rown * L + x0;
-        uint32_t U = Yd & ~((Yd & X & Xn) << 1);
+        uint32_t U = Yd & ~((Yd & X & Xn) << 1) & segmask;
         while (U) {
           const int b = __ffs(U) - 1;
           U &= U - 1u;
@@ -296,12 +306,13 @@ size_t small_layout_bytes_max() {
 
 uint32_t small_sites_limit(int model, int dim) {
   // measured on the GB300 against the tiled path (with its overlapped
-  // launches), µs per measured sweep at T_c: 2D Ising L = 64: 25.3 here,
-  // 27.1 tiled, L = 80: 31.1 here, 29.7 tiled; 2D Potts q = 4 L = 90: 32.3
-  // here, 38.2 tiled; 3D Ising L = 8: 17.4 here, 18.7 tiled, L = 12: 25.9
-  // here, 24.4 tiled; 3D Potts q = 3 L = 16: 37.9 here, 34.9 tiled
-  if (dim == 2) return model == kPotts ? (uint32_t)kSmallSites : 4096u;
-  return 1024u;
+  // launches), us per sweep at T_c over back-to-back sweeps: 2D Ising L = 80:
+  // 18.8 here, 28.6 tiled; L = 90: 26.8 here, 30.1 tiled; 3D Ising L = 12:
+  // 20.4 here, 23.1 tiled; L = 16: 24.3 here, 27.7 tiled; L = 20: 36.4 here,
+  // 33.2 tiled; 3D Potts q = 3 L = 16: 26.5 here, 31.7 tiled; L = 20: 40.3
+  // here, 37.4 tiled.  2D: the layout's whole capacity.
+  (void)model;
+  return dim == 2 ? (uint32_t)kSmallSites : 4096u;
 }
 
 bool small_lattice(const Lattice& lat) {

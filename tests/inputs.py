@@ -132,8 +132,8 @@ def ragged_batch(n: int = 256, seed: int = 1003):
 
 def small_batch(n: int = 256, seed: int = 1005):
     """Many small lattices: n 2D lattices, model uniform over {Ising, Potts
-    q=3, Potts q=4}, L uniform over [16, 90] (at most 8192 sites; the
-    one-CTA path takes Potts lattices up to 8192 sites, Ising up to 4096),
+    q=3, Potts q=4}, L uniform over [16, 90] (at most 8192 sites, all of
+    them within the one-CTA path's 2D limit),
     T uniform in [0.8 Tc, 1.2 Tc], one seed per lattice.
     Returns a list of (model, dim, L, q, T, seed)."""
     rng = np.random.default_rng(seed)

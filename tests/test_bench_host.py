@@ -71,7 +71,7 @@ def test_batch_launch_count():
     import inputs
     ising, potts = inputs.ISING, inputs.POTTS
     big = [(ising, 2, 1024, 2, 2.0, 1), (potts, 2, 512, 3, 1.0, 2)]
-    small = [(ising, 2, 32, 2, 2.0, 3), (potts, 2, 90, 4, 0.9, 4), (ising, 2, 80, 2, 2.0, 5)]
+    small = [(ising, 2, 32, 2, 2.0, 3), (potts, 2, 90, 4, 0.9, 4), (ising, 2, 100, 2, 2.0, 5)]
     assert bench.batch_launches(big, 0) == 2 + 3 + 1
     assert bench.batch_launches(big, 1) == 1 + 3 + 1
     # the grid form (bit 1) launches the same kernels; the merge split by
@@ -80,10 +80,10 @@ def test_batch_launch_count():
     assert bench.batch_launches(big, 3) == 1 + 3 + 1
     assert bench.batch_launches(big, 4) == 2 + 4 + 1
     assert bench.batch_launches([(ising, 3, 64, 2, 4.5, 7)], 5) == 1 + 5 + 1
-    # Ising L = 80 (6400 sites) is tiled, Potts L = 90 (8100) and Ising L = 32 are one-CTA
+    # Ising L = 100 (10000 sites) is tiled, Potts L = 90 (8100) and Ising L = 32 are one-CTA
     assert bench.batch_launches(small, 0) == 1 + 3 + 2 + 1
-    assert bench.batch_launches([(ising, 3, 10, 2, 4.5, 6)], 0) == 0 + 0 + 1 + 1
-    assert bench.batch_launches([(ising, 3, 11, 2, 4.5, 6)], 0) == 1 + 3 + 0 + 1
+    assert bench.batch_launches([(ising, 3, 16, 2, 4.5, 6)], 0) == 0 + 0 + 1 + 1
+    assert bench.batch_launches([(ising, 3, 17, 2, 4.5, 6)], 0) == 1 + 3 + 0 + 1
 
 
 def test_workload_recipes():

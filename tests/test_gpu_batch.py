@@ -230,7 +230,7 @@ def test_autotune_of_one_model_tries_one_schedule(sw):
 
 
 def test_small_members_run_whole_in_shared_memory(sw):
-    """Members of at most 4096 sites (2D Ising) or 8192 (2D Potts) take the one-CTA
+    """Members of at most 8192 sites (2D) take the one-CTA
     branch of the batch graph; a batch of many of them, Ising and Potts,
     with a large member beside them, stays bit-identical to every lattice
     advanced alone, across a member leaving."""

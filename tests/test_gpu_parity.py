@@ -77,14 +77,14 @@ def test_initial_state(sw, model, dim, L, q):
 @pytest.mark.parametrize("dim,L,T", [
     (2, 4, 2.269185), (2, 16, 2.269185), (2, 31, 2.0), (2, 48, 2.269185), (2, 64, 2.269185),
     (2, 100, 2.4), (2, 130, 1.8), (3, 4, 4.5), (3, 8, 4.5115), (3, 9, 4.0), (3, 33, 4.5115),
-    (3, 40, 5.0), (3, 64, 4.5115), (3, 11, 4.5115)])
+    (3, 40, 5.0), (3, 64, 4.5115), (3, 11, 4.5115), (3, 19, 4.5115)])
 def test_ising_sweeps_bit_exact(sw, dim, L, T):
     run_exact_parity(sw, ISING, dim, L, 2, T, seed=1000 + L, sweeps=12)
 
 
 @pytest.mark.parametrize("dim,L,q,T", [
     (2, 64, 3, 0.994973), (2, 48, 4, 0.910239), (2, 37, 8, 0.74), (2, 32, 256, 0.3),
-    (3, 16, 3, 1.8), (3, 24, 8, 1.3), (3, 15, 3, 1.8)])
+    (3, 16, 3, 1.8), (3, 24, 8, 1.3), (3, 15, 3, 1.8), (3, 19, 3, 1.8)])
 def test_potts_sweeps_bit_exact(sw, dim, L, q, T):
     run_exact_parity(sw, POTTS, dim, L, q, T, seed=2000 + L, sweeps=12)
 
