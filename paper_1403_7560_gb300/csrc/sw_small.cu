@@ -10,13 +10,16 @@
 // path (equality masks by warp ballots, a thread per row word and
 // direction for the Bernoulli words), step (2) the union-find of the tiled
 // path over the whole periodic lattice (every site's parent is its x-run
-// start, then a thread per row word joins the runs bonded to the next row
-// word and to the +y / +z rows; the smallest index becomes the root, so
-// labels are canonical), step (3) every site takes its root's draw (the
-// same draw definitions), and the new state is measured into the same
-// per-sweep record and FP64 accumulators.  After the last sweep the spins, that sweep's bond planes
-// and a forest of (root, marker, draw) words are written back, so every
-// readout call sees the same state as after tiled sweeps.
+// start, then threads per row word, one per range of its bits, join the
+// runs bonded to the +y / +z rows, one of them also the run bonded to the
+// next row word; the smallest index becomes the root, so labels are
+// canonical), step (3) every site takes its root's draw (the same draw
+// definitions), and the new state is measured into the same per-sweep
+// record and FP64 accumulators.  After the last sweep the spins, that
+// sweep's bond planes and a forest of (root, marker, draw) words are
+// written back, so every readout call sees the same state as after tiled
+// sweeps.  The whole lattice is on one SM, so every phase's slowest thread
+// holds the others at the next barrier: the unions are split for that.
 #include <string>
 
 #include "../../include/sw.h"
